@@ -1,0 +1,234 @@
+/*
+ * ann.h -- C ABI of libann: the online query path of GATE-style graph
+ * approximate nearest-neighbour search (arXiv 2506.15986) on one GB300
+ * (sm_103a).
+ *
+ * Conventions shared by every entry point
+ *  - Pointers named d_* are CUDA device pointers on the index's device; other
+ *    pointers are host pointers unless stated otherwise.  All device buffers
+ *    passed in are owned by the caller and must stay valid until the work
+ *    queued on `stream` has finished.  The index owns the device copies of its
+ *    base vectors, graph and entry model, and frees them in ann_free_index.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *    that take a stream are asynchronous: they validate their arguments on the
+ *    host, queue kernels and return.
+ *  - Errors in the arguments or files are returned synchronously before any
+ *    kernel is queued.  Conditions found on the device (visited-set capacity,
+ *    a bounded wait that timed out) are OR-ed into the index's device status
+ *    word; ann_sync_status returns and clears them.  Queries hit by such a
+ *    condition return ids -1 and distance +inf (INT32_MAX for uint8 data).
+ *  - Orders are lexicographic on (distance, id): ties go to the smaller id.
+ *  - Distances: uint8 data use exact int32 squared L2; floating-point data
+ *    accumulate squared L2, or the negated inner product for ANN_IP, in fp32.
+ */
+#ifndef ANN_H
+#define ANN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ANN_OK = 0,
+    ANN_ERR_INVALID_ARG = 1,
+    ANN_ERR_IO = 2,
+    ANN_ERR_FORMAT = 3,
+    ANN_ERR_OOM = 4,
+    ANN_ERR_CUDA = 5,
+    ANN_ERR_CAPACITY = 6,
+    ANN_ERR_TIMEOUT = 7,
+    ANN_ERR_UNSUPPORTED = 8
+} ann_status;
+
+/* element type of the stored base vectors */
+typedef enum { ANN_U8 = 0, ANN_F32 = 1, ANN_F16 = 2, ANN_BF16 = 3 } ann_dtype;
+
+/* ANN_L2: squared Euclidean distance; ANN_IP: -<q, x> (maximum inner product) */
+typedef enum { ANN_L2 = 0, ANN_IP = 1 } ann_metric;
+
+typedef struct ann_index ann_index;
+
+/* Search flags */
+#define ANN_SEARCH_RERANK 1u /* re-score the final pool from the fp32 copy (see ann_index_desc.base_f32) */
+
+/* Limits of one search */
+#define ANN_MAX_L 512      /* pool size L */
+#define ANN_MAX_W 4        /* entries expanded per step */
+#define ANN_MAX_STEP_CAND 64 /* W * degree */
+
+/*
+ * Index description for ann_index_create.  The path searches a fixed-degree
+ * proximity graph (Sec. 2.1, Def. 1) over base vectors D.
+ *   n, dim       number of base vectors and their dimension; dim * element
+ *                size must be a multiple of 16 bytes (16-byte row gathers)
+ *   degree       R, slots per adjacency row (R * ANN_MAX_W is capped by
+ *                ANN_MAX_STEP_CAND for W > 1)
+ *   dtype,metric see ann_dtype / ann_metric; uint8 supports ANN_L2 only
+ *   base         n*dim elements of dtype, row-major (host or device pointer)
+ *   graph        n*degree int32 node ids, row-major; -1 marks an unused
+ *                slot (host or device pointer)
+ *   medoid       entry node used when no per-query entry is given (the
+ *                navigating node of Sec. 2.1)
+ *   base_f32     optional n*dim fp32 rows (host or device) kept for the exact
+ *                rerank of reduced-precision (F16/BF16) storage; may be NULL
+ * The index copies everything it is given; the caller keeps ownership.
+ */
+typedef struct {
+    int64_t n;
+    int32_t dim;
+    int32_t degree;
+    int32_t dtype;
+    int32_t metric;
+    const void *base;
+    const int32_t *graph;
+    int32_t medoid;
+    const float *base_f32;
+} ann_index_desc;
+
+/*
+ * Per-call search parameters (Sec. 2.1, Algorithm 1: pool size l_s = L,
+ * result size k).
+ *   k         results per query, 1 <= k <= L; also the row stride of the
+ *             outputs when d_k is given (then every d_k[i] <= k)
+ *   L         pool size, 1 <= L <= ANN_MAX_L; the maximum when d_L is given
+ *   W         pool entries expanded per step, 1..ANN_MAX_W, W*degree <= 64
+ *   hash_bits log2 of the per-query shared-memory visited-table capacity,
+ *             0 = chosen from L; 8..15
+ *   flags     ANN_SEARCH_* bits
+ *   d_k, d_L  optional per-query k and L (device int32[nq]); NULL = k, L
+ *   d_target  optional per-query target node (device int32[nq]); when given
+ *             the search runs in label mode: it stops after the step in which
+ *             the target is evaluated and d_stats reports the counters at that
+ *             point (INT32_MAX when it never is; Sec. 4.2, Def. 4)
+ */
+typedef struct {
+    int32_t k;
+    int32_t L;
+    int32_t W;
+    int32_t hash_bits;
+    uint32_t flags;
+    const int32_t *d_k;
+    const int32_t *d_L;
+    const int32_t *d_target;
+} ann_search_params;
+
+/* Human-readable name of a status code (static storage; never NULL). */
+const char *ann_status_string(ann_status s);
+
+/*
+ * Create an index on CUDA device `device` from `desc` (copied into memory the
+ * index owns).  Validates sizes, dtype/metric and that every graph id is in
+ * [-1, n) and the medoid in [0, n).  Returns ANN_ERR_INVALID_ARG on bad
+ * arguments, ANN_ERR_OOM / ANN_ERR_CUDA on device failures; *out is set only
+ * on success.
+ */
+ann_status ann_index_create(const ann_index_desc *desc, int device, ann_index **out);
+
+/* Free an index and its device memory (NULL is accepted).  Synchronises the device. */
+ann_status ann_free_index(ann_index *idx);
+
+/*
+ * Read index metadata; any output pointer may be NULL.  has_model reports
+ * whether a learned entry model is attached.
+ */
+ann_status ann_index_info(const ann_index *idx, int64_t *n, int32_t *dim, int32_t *degree,
+                          int32_t *dtype, int32_t *metric, int32_t *medoid,
+                          int32_t *n_hubs, int32_t *has_model);
+
+/*
+ * Write the index (header, base, graph, optional fp32 copy, entry model) to
+ * `path` with a 64-bit FNV-1a checksum.  ANN_ERR_IO on a write failure.
+ */
+ann_status ann_save_index(const ann_index *idx, const char *path);
+
+/*
+ * Load an index written by ann_save_index onto `device`.  ANN_ERR_IO if the
+ * file cannot be read, ANN_ERR_FORMAT if its magic, version, sizes or checksum
+ * do not match (a truncated or corrupted file).
+ */
+ann_status ann_load_index(const char *path, int device, ann_index **out);
+
+/*
+ * Batched best-first beam search (Sec. 2.1, Algorithm 1; sorted-pool form):
+ * for each query, start from its entry node, repeatedly expand the first W
+ * unexpanded entries of a pool of the L best nodes seen, evaluate every
+ * unvisited neighbour once, and stop when the pool holds no unexpanded entry.
+ *   d_queries nq*dim query rows: uint8 for an ANN_U8 index, fp32 otherwise
+ *   nq        number of queries (0 is accepted and queues nothing)
+ *   d_entry   per-query entry node (device int32[nq]) or NULL for the medoid
+ *   p         search parameters (host pointer)
+ *   d_ids     out: nq*k int32 node ids, best first; -1 pads missing results
+ *   d_dists   out: nq*k distances, int32 for ANN_U8 and fp32 otherwise
+ *   d_stats   out (optional): nq*2 int32 {distance evaluations, expansions}
+ * One warp serves one query; queries are pulled from a device work queue by
+ * a persistent grid sized to the SM count.  Scratch memory is taken from a
+ * stream-ordered pool owned by the index.
+ */
+ann_status ann_search_batch(ann_index *idx, const void *d_queries, int64_t nq,
+                            const int32_t *d_entry, const ann_search_params *p,
+                            int32_t *d_ids, void *d_dists, int32_t *d_stats, void *stream);
+
+/*
+ * Synchronise `stream`, then return and clear the index's device status
+ * word: ANN_OK, or the first of ANN_ERR_CAPACITY / ANN_ERR_TIMEOUT raised by
+ * kernels since the last call; ANN_ERR_CUDA if a CUDA call failed.
+ */
+ann_status ann_sync_status(ann_index *idx, void *stream);
+
+/* ---- offline construction (GPU) ------------------------------------------ */
+
+/*
+ * Exact k nearest neighbours (Sec. 2.1, Problem 1; the ground truth R of
+ * recall@k): for each of nq query rows, the k base rows with the smallest
+ * (distance, id).  Candidate scores come from an fp32 GEMM; the best k + margin
+ * candidates per query are re-scored exactly (int32 for uint8, fp32 direct
+ * differences otherwise) and sorted.
+ *   d_base       n*dim base rows (dtype ANN_U8 or ANN_F32), 16-byte aligned
+ *   d_queries    nq*dim rows of the same dtype; equal to d_base when
+ *                exclude_self != 0 (then row i never returns id i)
+ *   k            1..128 and <= n
+ *   d_ids,d_dists out: nq*k int32 ids and distances (int32 for ANN_U8, fp32
+ *                otherwise)
+ * Blocking: returns after the results are written.  Temporary device memory
+ * (about 4 GiB of scores plus fp32 copies of uint8 rows) is allocated on
+ * `stream` and released before returning.
+ */
+ann_status ann_knn(const void *d_base, int64_t n, int32_t dim, int32_t dtype, int32_t metric,
+                   const void *d_queries, int64_t nq, int32_t k, int32_t exclude_self,
+                   int32_t *d_ids, void *d_dists, void *stream);
+
+/*
+ * Navigating node (Sec. 2.1, NSG): argmin_i ||x_i - mean||^2, smaller id on
+ * ties.  uint8 rows are handled exactly in 64-bit integers (n <= 2^20,
+ * dim <= 128); fp32 rows in fp32.  Blocking.
+ */
+ann_status ann_medoid(const void *d_base, int64_t n, int32_t dim, int32_t dtype, int32_t *medoid,
+                      void *stream);
+
+/*
+ * Proximity graph (Sec. 2.1, Def. 1) under squared L2:
+ *  1. the K exact nearest other nodes of every node, by (distance, id);
+ *  2. relative-neighbourhood pruning in that order: candidate c is kept unless
+ *     a node s kept before it has alpha * delta(s, c) <= delta(p, c); at most
+ *     R are kept; -1 pads the row;
+ *  3. reachability repair from the navigating node: nodes are taken in id
+ *     order; an unreachable node u gets the edge w -> u from the reachable node
+ *     w nearest to u (by (distance, id)) whose row has a free slot, and every
+ *     node reachable from u becomes reachable before the next node is taken.
+ *   d_graph   out: n*R int32 adjacency rows (device)
+ *   medoid    in/out: the navigating node; a negative value asks for the medoid
+ *   repairs   out (optional): number of edges added in step 3
+ * Blocking.  ANN_ERR_CAPACITY if step 3 finds no reachable node with a free
+ * slot.  Requires K <= 128, R <= min(K, 64) and dim*elem*K <= 160 KiB.
+ */
+ann_status ann_build_graph(const void *d_base, int64_t n, int32_t dim, int32_t dtype, int32_t K,
+                           int32_t R, float alpha, int32_t *d_graph, int32_t *medoid,
+                           int64_t *repairs, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ANN_H */

@@ -278,3 +278,20 @@ def labels_from_costs(evals, hops, cand, n_hubs, t_pos=3, t_neg=15):
             else:
                 mask[i, h] = 0
     return mask, best
+
+
+def pruned_row(base, p, K, R, alpha=1.0):
+    """Steps 1-2 of the graph builder (Sec. 2.1, Def. 1) for the single node p:
+    its K exact nearest other nodes by (dist, id), then relative-neighbourhood
+    pruning in that order (c kept unless a kept s has alpha*d(s,c) <= d(p,c)),
+    at most R kept.  Distances in float64."""
+    b = np.asarray(base)
+    x = b.astype(np.float64) if b.dtype != np.float64 else b
+    ids, dists = knn(b, x[p:p + 1], K, exclude=[p])
+    kept = []
+    for c, dpc in zip(ids[0].tolist(), dists[0].tolist()):
+        if c < 0 or len(kept) == R:
+            break
+        if all(alpha * float(((x[s] - x[c]) ** 2).sum()) > dpc for s in kept):
+            kept.append(c)
+    return kept

@@ -1,0 +1,197 @@
+"""Thin Python binding of libann's C ABI (``include/ann.h``).
+
+Argument marshalling only: every function here forwards to the entry point of
+the same name in ``libann.so`` and raises ``AnnError`` on a non-OK status.
+Device buffers are passed as ``torch.Tensor`` (CUDA) or raw integer pointers;
+streams as ``torch.cuda.Stream`` or raw ``cudaStream_t`` integers.  There is no
+fallback: if the library cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libann.so")
+
+# ann_status
+OK, ERR_INVALID_ARG, ERR_IO, ERR_FORMAT, ERR_OOM, ERR_CUDA, ERR_CAPACITY, ERR_TIMEOUT, ERR_UNSUPPORTED = range(9)
+# ann_dtype / ann_metric
+U8, F32, F16, BF16 = 0, 1, 2, 3
+L2, IP = 0, 1
+SEARCH_RERANK = 1
+MAX_L, MAX_W, MAX_STEP_CAND = 512, 4, 64
+
+_c = ctypes
+_p = ctypes.c_void_p
+
+
+class ann_index_desc(ctypes.Structure):
+    _fields_ = [("n", _c.c_int64), ("dim", _c.c_int32), ("degree", _c.c_int32),
+                ("dtype", _c.c_int32), ("metric", _c.c_int32), ("base", _p),
+                ("graph", _p), ("medoid", _c.c_int32), ("base_f32", _p)]
+
+
+class ann_search_params(ctypes.Structure):
+    _fields_ = [("k", _c.c_int32), ("L", _c.c_int32), ("W", _c.c_int32),
+                ("hash_bits", _c.c_int32), ("flags", _c.c_uint32), ("d_k", _p),
+                ("d_L", _p), ("d_target", _p)]
+
+
+class AnnError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} ({status})")
+
+
+_LIB = None
+
+
+def load_library(path: str | None = None):
+    """Load libann.so (built by ``_build.build()``); raises if it is missing."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise OSError(f"libann.so not found at {path}; run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    i32, i64 = _c.c_int32, _c.c_int64
+    pp = _c.POINTER(_p)
+    sig = {
+        "ann_status_string": ([i32], _c.c_char_p),
+        "ann_index_create": ([_c.POINTER(ann_index_desc), i32, pp], i32),
+        "ann_free_index": ([_p], i32),
+        "ann_index_info": ([_p] + [_p] * 8, i32),
+        "ann_save_index": ([_p, _c.c_char_p], i32),
+        "ann_load_index": ([_c.c_char_p, i32, pp], i32),
+        "ann_search_batch": ([_p, _p, i64, _p, _c.POINTER(ann_search_params), _p, _p, _p, _p], i32),
+        "ann_sync_status": ([_p, _p], i32),
+        "ann_knn": ([_p, i64, i32, i32, i32, _p, i64, i32, i32, _p, _p, _p], i32),
+        "ann_medoid": ([_p, i64, i32, i32, _c.POINTER(i32), _p], i32),
+        "ann_build_graph": ([_p, i64, i32, i32, i32, i32, _c.c_float, _p, _c.POINTER(i32),
+                             _c.POINTER(i64), _p], i32),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _LIB = lib
+    return lib
+
+
+def status_string(s: int) -> str:
+    return load_library().ann_status_string(int(s)).decode()
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError(f"cannot take a pointer of {type(x)}")
+
+
+def _stream(s):
+    if s is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _check(st, where):
+    if st != OK:
+        raise AnnError(st, where)
+
+
+def ann_index_create(base, graph, medoid, dtype, metric=L2, device=0, base_f32=None,
+                     n=None, dim=None, degree=None):
+    """Create an index from host (numpy) or device (torch) arrays; returns a handle."""
+    if n is None:
+        n, dim = base.shape
+        degree = graph.shape[1]
+    d = ann_index_desc(n=int(n), dim=int(dim), degree=int(degree), dtype=int(dtype),
+                       metric=int(metric), base=_ptr(base), graph=_ptr(graph),
+                       medoid=int(medoid), base_f32=_ptr(base_f32))
+    h = _p()
+    _check(load_library().ann_index_create(ctypes.byref(d), int(device), ctypes.byref(h)),
+           "ann_index_create")
+    return h.value
+
+
+def ann_free_index(h):
+    _check(load_library().ann_free_index(h), "ann_free_index")
+
+
+def ann_index_info(h):
+    vals = [_c.c_int64()] + [_c.c_int32() for _ in range(7)]
+    _check(load_library().ann_index_info(h, *[ctypes.byref(v) for v in vals]), "ann_index_info")
+    keys = ["n", "dim", "degree", "dtype", "metric", "medoid", "n_hubs", "has_model"]
+    return {k: v.value for k, v in zip(keys, vals)}
+
+
+def ann_save_index(h, path):
+    _check(load_library().ann_save_index(h, os.fsencode(path)), "ann_save_index")
+
+
+def ann_load_index(path, device=0):
+    h = _p()
+    _check(load_library().ann_load_index(os.fsencode(path), int(device), ctypes.byref(h)),
+           "ann_load_index")
+    return h.value
+
+
+def search_params(k, L, W=1, hash_bits=0, flags=0, d_k=None, d_L=None, d_target=None):
+    return ann_search_params(k=int(k), L=int(L), W=int(W), hash_bits=int(hash_bits),
+                             flags=int(flags), d_k=_ptr(d_k), d_L=_ptr(d_L),
+                             d_target=_ptr(d_target))
+
+
+def ann_search_batch(h, queries, nq, entry, params, ids, dists, stats=None, stream=None):
+    """Queue the batched beam search; outputs land in the caller's buffers."""
+    _check(load_library().ann_search_batch(h, _ptr(queries), int(nq), _ptr(entry),
+                                           ctypes.byref(params), _ptr(ids), _ptr(dists),
+                                           _ptr(stats), _stream(stream)),
+           "ann_search_batch")
+
+
+def ann_sync_status(h, stream=None):
+    """Synchronise the stream and return the device status (0 = OK)."""
+    return int(load_library().ann_sync_status(h, _stream(stream)))
+
+
+def ann_knn(base, n, dim, dtype, metric, queries, nq, k, ids, dists, exclude_self=False,
+            stream=None):
+    """Exact k-NN on the GPU (blocking); outputs in the caller's device buffers."""
+    _check(load_library().ann_knn(_ptr(base), int(n), int(dim), int(dtype), int(metric),
+                                  _ptr(queries), int(nq), int(k), int(bool(exclude_self)),
+                                  _ptr(ids), _ptr(dists), _stream(stream)), "ann_knn")
+
+
+def ann_medoid(base, n, dim, dtype, stream=None) -> int:
+    m = _c.c_int32(-1)
+    _check(load_library().ann_medoid(_ptr(base), int(n), int(dim), int(dtype), ctypes.byref(m),
+                                     _stream(stream)), "ann_medoid")
+    return m.value
+
+
+def ann_build_graph(base, n, dim, dtype, K, R, alpha, graph, medoid=-1, stream=None):
+    """Build the proximity graph on the GPU (blocking).  Returns (medoid, repairs)."""
+    m = _c.c_int32(int(medoid))
+    rep = _c.c_int64(0)
+    _check(load_library().ann_build_graph(_ptr(base), int(n), int(dim), int(dtype), int(K),
+                                          int(R), float(alpha), _ptr(graph), ctypes.byref(m),
+                                          ctypes.byref(rep), _stream(stream)),
+           "ann_build_graph")
+    return m.value, rep.value

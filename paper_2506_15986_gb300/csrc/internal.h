@@ -1,0 +1,66 @@
+// internal.h -- host-side index object and kernel launchers of libann.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ann.h"
+
+struct ann_entry_model;  // learned entry selection (entry.cu)
+
+struct ann_index {
+    int device = 0;
+    int num_sms = 0;
+    int64_t n = 0;
+    int32_t dim = 0;
+    int32_t degree = 0;
+    int32_t dtype = ANN_F32;
+    int32_t metric = ANN_L2;
+    int32_t medoid = 0;
+    int32_t rowbytes = 0;  // bytes of one stored base row
+    void *d_base = nullptr;
+    int32_t *d_graph = nullptr;
+    float *d_base_f32 = nullptr;  // optional exact copy for rerank
+    int *d_status = nullptr;      // device status word (kStatus* bits)
+    cudaMemPool_t pool = nullptr; // stream-ordered scratch
+    ann_entry_model *model = nullptr;
+};
+
+namespace ann {
+
+// device status bits, OR-ed into the index's status word by kernels
+constexpr int kStatusCapacityBit = 1;
+constexpr int kStatusTimeoutBit = 2;
+constexpr int kStatusBadInputBit = 4;
+
+int elem_size(int dtype);
+
+// status helpers
+ann_status cuda_status(cudaError_t e);
+
+// Scratch from the index's stream-ordered pool.
+ann_status scratch_alloc(ann_index *idx, size_t bytes, cudaStream_t s, void **out);
+void scratch_free(ann_index *idx, void *p, cudaStream_t s);
+
+struct SearchLaunch {
+    const void *queries;
+    int qbytes;  // bytes of one query row
+    int64_t nq;
+    const int32_t *entries;  // nullptr = medoid
+    const ann_search_params *p;
+    int32_t *ids;
+    void *dists;
+    int32_t *stats;
+    // optional caller-provided scratch: work counter (8 bytes) + spill tables
+    void *scratch;
+    size_t scratch_bytes;
+    int max_teams;  // cap on the persistent grid (0 = occupancy-limited only)
+};
+
+// Queues the beam-search kernel (search.cu).
+ann_status launch_search(ann_index *idx, const SearchLaunch &L, cudaStream_t s);
+
+// Scratch bytes launch_search needs for `teams` teams at the given params.
+size_t search_scratch_bytes(int teams, int spill_bits);
+
+}  // namespace ann

@@ -1,0 +1,183 @@
+"""GPU parity of the batched beam search (Sec. 2.1, Algorithm 1) against the
+CPU oracle, through the C ABI.
+
+uint8 data: ids, int32 distances, evaluation and expansion counts bit-exact.
+fp32 data: >= 99.9% of (query, rank) ids equal, distances within 1e-5
+relative (1e-5 of |x||q| for inner product), recall@10 within 0.001."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2506_15986_gb300 import ann, synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from gpu_util import make_index, search  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2506_15986_gb300 import _build
+    _build.build()
+    ann.load_library()
+
+
+@pytest.fixture(scope="module")
+def c1():
+    w = synth.small_u8()
+    g, _ = oracle.build_graph(w["base"], K=64, R=32, alpha=1.0)
+    med = oracle.medoid(w["base"])
+    h = make_index(w["base"], g, med)
+    yield dict(w, graph=g, medoid=med, h=h)
+    ann.ann_free_index(h)
+
+
+def _oracle(w, q, L, k, **kw):
+    return oracle.search(w["base"], w["graph"], np.asarray(q, np.float64),
+                         kw.pop("entries", w["medoid"]), L, k, **kw)
+
+
+def test_toy_graphs_exact(golden_dir):
+    with open(os.path.join(golden_dir, "toy_graphs.json")) as f:
+        cases = json.load(f)["cases"]
+    for c in cases:
+        pts = np.asarray(c["points"], np.float32)
+        pad = np.zeros((len(pts), 4), np.float32)
+        pad[:, : pts.shape[1]] = pts  # zero padding keeps squared L2 unchanged
+        q = np.zeros((1, 4), np.float32)
+        q[0, : pts.shape[1]] = c["query"]
+        h = make_index(pad, np.asarray(c["adjacency"], np.int32), c["entry"])
+        try:
+            ids, d, ev, hp, st = search(h, q, c["k"], c["L"], W=c["W"])
+        finally:
+            ann.ann_free_index(h)
+        assert st == ann.OK
+        assert ids[0].tolist() == c["ids"], c["name"]
+        exp = [math.inf if v == "inf" else float(v) for v in c["dists"]]
+        assert d[0].tolist() == exp, c["name"]
+        assert (int(ev[0]), int(hp[0])) == (c["evals"], c["hops"]), c["name"]
+
+
+@pytest.mark.parametrize("L,W", [(64, 1), (16, 1), (128, 1), (64, 2), (512, 2), (10, 1)])
+def test_c1_u8_bit_exact(c1, L, W):
+    q = c1["queries"]
+    k = min(10, L)
+    ids, d, ev, hp, st = search(c1["h"], q, k, L, W=W)
+    oi, od, oe, oh = _oracle(c1, q, L, k, W=W)
+    assert st == ann.OK
+    assert np.array_equal(ids, oi)
+    assert np.array_equal(d, od.astype(np.int64).clip(max=2**31 - 1).astype(np.int32))
+    assert np.array_equal(ev, oe) and np.array_equal(hp, oh)
+
+
+def test_c1_spill_to_global_table_stays_exact(c1):
+    # hash_bits=8: 192 shared slots, far fewer than the evaluations, so the
+    # exact global spill table carries most of the visited set
+    q = c1["queries"]
+    ids, d, ev, hp, st = search(c1["h"], q, 10, 128, hash_bits=8)
+    oi, od, oe, oh = _oracle(c1, q, 128, 10)
+    assert st == ann.OK
+    assert (oe > 192).mean() > 0.8  # most queries outgrow the shared table
+    assert np.array_equal(ids, oi) and np.array_equal(ev, oe) and np.array_equal(hp, oh)
+
+
+def test_c1_per_query_entries_k_L(c1):
+    rng = np.random.default_rng(3)
+    q = c1["queries"]
+    nq = len(q)
+    entries = rng.integers(0, len(c1["base"]), nq).astype(np.int32)
+    Ls = rng.integers(10, 200, nq).astype(np.int32)
+    ks = np.minimum(rng.integers(1, 11, nq), Ls).astype(np.int32)
+    ids, d, ev, hp, st = search(c1["h"], q, 10, 200, entries=entries, ks=ks, Ls=Ls)
+    oi, od, oe, oh = oracle.search(c1["base"], c1["graph"], q.astype(np.float64), entries, 0, 0,
+                                   Ls=Ls, ks=ks)
+    assert st == ann.OK
+    oi_full = np.full((nq, 10), -1, np.int32)
+    oi_full[:, : oi.shape[1]] = oi
+    assert np.array_equal(ids, oi_full)
+    assert np.array_equal(ev, oe) and np.array_equal(hp, oh)
+
+
+def test_c1_label_mode_targets(c1):
+    q = c1["queries"][:50]
+    t, _ = oracle.knn(c1["base"], q.astype(np.float64), 1)
+    rng = np.random.default_rng(5)
+    entries = rng.integers(0, len(c1["base"]), 50).astype(np.int32)
+    entries[0] = t[0, 0]  # entry is the target: 1 evaluation, 0 expansions
+    ids, d, ev, hp, st = search(c1["h"], q, 1, 64, entries=entries, targets=t[:, 0])
+    _, _, oe, oh = oracle.search(c1["base"], c1["graph"], q.astype(np.float64), entries, 64, 1,
+                                 targets=t[:, 0])
+    assert st == ann.OK
+    assert np.array_equal(ev, oe) and np.array_equal(hp, oh)
+    assert (ev[0], hp[0]) == (1, 0)
+
+
+def test_empty_batch_and_bad_device_inputs(c1):
+    q = c1["queries"]
+    ids, d, ev, hp, st = search(c1["h"], q[:0], 10, 64)
+    assert ids.shape == (0, 10) and st == ann.OK
+    # a per-query L above the launch maximum is reported, never read past
+    ids, d, ev, hp, st = search(c1["h"], q[:4], 10, 64, Ls=np.array([64, 65, 64, 64]))
+    assert st == ann.ERR_INVALID_ARG
+    assert (ids[1] == -1).all() and (ids[0] >= 0).all()
+    assert ann.ann_sync_status(c1["h"]) == ann.OK  # cleared by the read
+
+
+@pytest.fixture(scope="module")
+def f32_case():
+    w = synth.shift_f32(n=20000, nq=300, n_train=0)
+    g, _ = oracle.build_graph(w["base"], K=64, R=32)
+    med = oracle.medoid(w["base"])
+    h = make_index(w["base"], g, med)
+    yield dict(w, graph=g, medoid=med, h=h)
+    ann.ann_free_index(h)
+
+
+def _f32_parity(ids, d, oi, od, truth, scale=None):
+    agree = (ids == oi).mean()
+    assert agree >= 0.999, agree
+    ok = ids == oi
+    ref = np.abs(od) if scale is None else scale[:, None].repeat(od.shape[1], 1)
+    rel = np.abs(d.astype(np.float64) - od)[ok] / np.maximum(ref[ok], 1e-30)
+    assert rel.max() <= 1e-5, rel.max()
+    r_gpu = oracle.recall_at_k(ids, truth, 10)
+    r_or = oracle.recall_at_k(oi, truth, 10)
+    assert abs(r_gpu - r_or) <= 1e-3
+
+
+@pytest.mark.parametrize("L,W", [(32, 1), (64, 1), (128, 2)])
+def test_f32_l2_parity(f32_case, L, W):
+    q = f32_case["queries"]
+    ids, d, ev, hp, st = search(f32_case["h"], q, 10, L, W=W)
+    oi, od, oe, oh = _oracle(f32_case, q, L, 10, W=W)
+    truth, _ = oracle.knn(f32_case["base"], q.astype(np.float64), 10)
+    assert st == ann.OK
+    _f32_parity(ids, d, oi, od, truth)
+    assert (ev == oe).mean() >= 0.99 and (hp == oh).mean() >= 0.99
+
+
+def test_f32_ip_parity():
+    w = synth.ip_f32(n=12000, nq=200)
+    base = w["base"]
+    # graph built on L2 over unit vectors (same order as IP for unit norms)
+    g, _ = oracle.build_graph(base, K=48, R=32)
+    med = oracle.medoid(base)
+    h = make_index(base, g, med, metric=ann.IP)
+    try:
+        q = w["queries"]
+        ids, d, ev, hp, st = search(h, q, 10, 64)
+    finally:
+        ann.ann_free_index(h)
+    oi, od, oe, oh = oracle.search(base, g, q.astype(np.float64), med, 64, 10, metric=oracle.IP)
+    truth, _ = oracle.knn(base, q.astype(np.float64), 10, metric=oracle.IP)
+    scale = np.linalg.norm(q.astype(np.float64), axis=1)  # |x| = 1
+    assert st == ann.OK
+    _f32_parity(ids, d, oi, od, truth, scale=scale)
