@@ -177,6 +177,177 @@ ann_status ann_search_batch(ann_index *idx, const void *d_queries, int64_t nq,
  */
 ann_status ann_sync_status(ann_index *idx, void *stream);
 
+/* ---- learned entry selection (Sec. 4.3) ---------------------------------- */
+
+/* How ann_select_entry picks each query's entry node. */
+typedef enum {
+    ANN_ENTRY_MEDOID = 0,             /* the index's navigating node */
+    ANN_ENTRY_LEARNED_NAV = 1,        /* greedy search of the hub graph (Algorithm 1, IP) */
+    ANN_ENTRY_LEARNED_EXHAUSTIVE = 2  /* argmax over every hub */
+} ann_entry_mode;
+
+/*
+ * Two-tower entry model (Sec. 2.2, Sec. 4.3).  Query tower: q_hat =
+ * normalise(ReLU(q W1 + b1) W2 + b2); hub tower: e_hat_v = normalise(e_v).
+ * The entry of q is the hub node of argmax_v q_hat . e_hat_v (cosine).
+ *   in_dim      query dimension; must equal the index dim (<= 512)
+ *   hidden      256; out_dim 64 (the only widths supported)
+ *   W1 [in_dim][256], b1 [256], W2 [256][64], b2 [64]: fp32, row-major
+ *   n_hubs      H >= 2; hub_nodes [H] node ids; hub_emb [H][64] fp32
+ *   hub_degree  s, 1..32 and < H: the high-tier graph links every hub to its
+ *               s most cosine-similar hubs (Sec. 4.3)
+ *   hub_graph   [H][s] int32, or NULL to build it from hub_emb (ties: smaller
+ *               hub index)
+ *   hub_entry   entry hub of the hub-graph search, or -1 for the hub with the
+ *               largest cosine to the mean embedding
+ * All arrays may be host or device pointers; they are copied.
+ */
+typedef struct {
+    int32_t in_dim;
+    int32_t hidden;
+    int32_t out_dim;
+    const float *W1;
+    const float *b1;
+    const float *W2;
+    const float *b2;
+    int32_t n_hubs;
+    const int32_t *hub_nodes;
+    const float *hub_emb;
+    int32_t hub_degree;
+    const int32_t *hub_graph;
+    int32_t hub_entry;
+} ann_entry_model_desc;
+
+/*
+ * Attach (or replace) the entry model of an index.  Builds the BF16 weight
+ * and embedding tables, the hub graph when not given, and the hub-graph
+ * index.  Blocking.  ANN_ERR_INVALID_ARG on bad sizes or hub node ids.
+ */
+ann_status ann_set_entry_model(ann_index *idx, const ann_entry_model_desc *model, void *stream);
+
+/*
+ * Copy the attached model out (host or device destinations; NULL skips an
+ * array).  Sizes as in ann_entry_model_desc.  ANN_ERR_INVALID_ARG without a model.
+ */
+ann_status ann_get_entry_model(const ann_index *idx, float *W1, float *b1, float *W2, float *b2,
+                               float *hub_emb, int32_t *hub_nodes, int32_t *hub_graph,
+                               int32_t *hub_entry);
+
+/*
+ * Entry node per query (Sec. 4.3: the recommended hub is the entry point).
+ *   d_queries  nq*dim rows as for ann_search_batch (16-byte aligned)
+ *   mode       ann_entry_mode; the learned modes need an attached model
+ *              (ANN_ERR_UNSUPPORTED otherwise)
+ *   L_hub      pool size of the hub-graph search (ANN_ENTRY_LEARNED_NAV), 1..512
+ *   d_entry    out: nq int32 node ids, ready for ann_search_batch
+ *   d_qhat     out (optional): nq*64 fp32 normalised query embeddings
+ * Asynchronous on `stream`; the query tower and the exhaustive hub scores run
+ * as BF16 tcgen05 GEMMs with FP32 accumulation.
+ */
+ann_status ann_select_entry(ann_index *idx, const void *d_queries, int64_t nq, int32_t mode,
+                            int32_t L_hub, int32_t *d_entry, float *d_qhat, void *stream);
+
+/* ---- entry-model training (Sec. 4.2 labels, Sec. 4.3 loss, Sec. 5.1 Adam) -- */
+
+typedef struct ann_trainer ann_trainer;
+
+/*
+ * Trainer of the two-tower model on one device.  Parameters start from the
+ * given fp32 arrays (host or device; W1 [in_dim][256], b1 [256], W2 [256][64],
+ * b2 [64], hub_emb [n_hubs][64]); Adam state starts at zero.
+ *   max_batch  largest batch (rows of scratch; the paper uses 8,192)
+ *   tau        InfoNCE temperature; lr, beta1, beta2, eps: Adam
+ * Every GEMM of a step runs on the tensor cores (BF16 operands, FP32
+ * accumulators); parameters, gradients and Adam state are fp32.
+ */
+ann_status ann_trainer_create(int device, int32_t in_dim, int32_t n_hubs, const float *W1, const float *b1,
+                              const float *W2, const float *b2, const float *hub_emb, int64_t max_batch,
+                              float tau, float lr, float beta1, float beta2, float eps, ann_trainer **out);
+
+ann_status ann_trainer_free(ann_trainer *t);
+
+/*
+ * One step on the batch of rows d_rows[0..nb) of d_queries (fp32, in_dim
+ * columns, 16-byte aligned); d_mask holds one label row of n_hubs int8 per
+ * query row (+1 positive, -1 negative, 0 unused).  Computes the loss and the
+ * gradients of every parameter; applies the Adam update when apply_update is
+ * non-zero.  loss_out (host, optional) receives the batch loss (blocking).
+ */
+ann_status ann_trainer_step(ann_trainer *t, const float *d_queries, const int32_t *d_rows, int64_t nb,
+                            const int8_t *d_mask, int32_t apply_update, float *loss_out, void *stream);
+
+/*
+ * Epochs of steps over nt training queries; epoch e visits rows
+ * d_order[e*nt .. e*nt+nt) (device, NULL = 0..nt-1) in batches of max_batch.
+ * d_losses (device, optional) receives epochs * ceil(nt / max_batch) batch
+ * losses.  Blocking.
+ */
+ann_status ann_trainer_fit(ann_trainer *t, const float *d_queries, int64_t nt, const int8_t *d_mask,
+                           const int32_t *d_order, int32_t epochs, float *d_losses, void *stream);
+
+/* Copy the current parameters (gradients != 0: the last step's gradients). */
+ann_status ann_trainer_get(const ann_trainer *t, float *W1, float *b1, float *W2, float *b2, float *hub_emb,
+                           int32_t gradients);
+
+/* Attach the trained model to an index (see ann_set_entry_model). */
+ann_status ann_trainer_attach(const ann_trainer *t, ann_index *idx, const int32_t *hub_nodes,
+                              int32_t hub_degree, void *stream);
+
+/*
+ * One Adam update with bias correction at step `step` (>= 1) over n fp32
+ * parameters: m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
+ * p -= lr (m / (1-b1^step)) / (sqrt(v / (1-b2^step)) + eps).  Asynchronous.
+ */
+ann_status ann_adam_update(float *d_params, const float *d_grads, float *d_m, float *d_v, int64_t n, int64_t step,
+                           float lr, float beta1, float beta2, float eps, void *stream);
+
+/* ---- hubs and labels --------------------------------------------------- */
+
+/*
+ * Lloyd's k-means (a flat stand-in for the balanced clustering of Sec. 4.1,
+ * Algorithm 2) on the sample rows sample_rows[0..m) (host int64) of d_x:
+ * centroids start at sample rows init[0..k) (host, indices into the sample);
+ * each iteration assigns every sample row to its nearest centroid by
+ * (squared L2, centroid index), then moves each centroid to its members'
+ * mean; an empty centroid moves onto the sample row farthest from its own
+ * centroid (larger distance first, smaller row on ties), each row used once.
+ *   d_centroids out: k*dim fp32; objective (host, optional): iters sums of
+ *   squared distances of the assignments.  Blocking.
+ */
+ann_status ann_kmeans(const void *d_x, int64_t n, int32_t dim, int32_t dtype, const int64_t *sample_rows,
+                      int64_t m, int32_t k, const int32_t *init, int32_t iters, float *d_centroids,
+                      double *objective, void *stream);
+
+/*
+ * Hub nodes (Sec. 4.1, Def. 3): assign every base row to its nearest centroid;
+ * d_hubs[j] = the member of cluster j nearest its centroid (smaller id on
+ * ties), -1 for an empty cluster.  d_assign (optional, n int32).  Blocking.
+ */
+ann_status ann_assign_hubs(const void *d_base, int64_t n, int32_t dim, int32_t dtype, const float *d_centroids,
+                           int32_t k, int32_t *d_hubs, int32_t *d_assign, void *stream);
+
+/*
+ * Label-mode search costs (Sec. 4.2, Def. 4): for query i and candidate hub
+ * d_cand[i*M + j], search from node d_hub_nodes[d_cand[i*M + j]] with pool L
+ * and width W until d_targets[i] (the query's exact nearest neighbour) is
+ * evaluated; d_evals / d_hops (nq*M) receive the counters after that step, or
+ * INT32_MAX when the target is never evaluated.  Asynchronous.
+ */
+ann_status ann_hub_costs(ann_index *idx, const void *d_queries, int64_t nq, const int32_t *d_targets,
+                         const int32_t *d_cand, int32_t M, const int32_t *d_hub_nodes, int32_t L, int32_t W,
+                         int32_t *d_evals, int32_t *d_hops, void *stream);
+
+/*
+ * Label rule per query over its M searched hubs: best = argmin (evals, hops,
+ * hub index) (-1 if none reached the target); m = min hops; label +1 if
+ * hops <= m + t_pos, -1 if hops >= m + t_neg or never reached, 0 otherwise;
+ * hubs not searched are -1; a query with no reached hub gets an all -1 row.
+ *   d_mask out: nq*n_hubs int8; d_best out (optional): nq int32.  Asynchronous.
+ */
+ann_status ann_hub_labels(const int32_t *d_evals, const int32_t *d_hops, const int32_t *d_cand, int64_t nq,
+                          int32_t M, int32_t n_hubs, int32_t t_pos, int32_t t_neg, int8_t *d_mask,
+                          int32_t *d_best, void *stream);
+
 /* ---- offline construction (GPU) ------------------------------------------ */
 
 /*

@@ -23,11 +23,25 @@ def relu(x):
     return np.maximum(x, 0.0)
 
 
-def tower_forward(X, W1, b1, W2, b2):
-    """Query tower forward pass; returns (q_hat, cache)."""
+def bf16_round(x):
+    """Round to the nearest bfloat16 (ties to even), returned as float64.
+
+    The paper fixes no precision; the tensor-core path takes its GEMM operands
+    (queries, weights, the hidden layer, embeddings) in bfloat16, so parity
+    tests feed this oracle the same rounded operands."""
+    u = np.asarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def tower_forward(X, W1, b1, W2, b2, round_hidden=None):
+    """Query tower forward pass; returns (q_hat, cache).  round_hidden, if
+    given, is applied to the hidden activations before the second layer."""
     X = np.asarray(X, np.float64)
     Z1 = X @ W1 + b1
     A1 = relu(Z1)
+    if round_hidden is not None:
+        A1 = round_hidden(A1)
     Z2 = A1 @ W2 + b2
     n = np.sqrt(np.sum(Z2 * Z2, axis=1, keepdims=True))
     Qh = Z2 / n

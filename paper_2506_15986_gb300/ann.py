@@ -38,6 +38,16 @@ class ann_search_params(ctypes.Structure):
                 ("d_L", _p), ("d_target", _p)]
 
 
+class ann_entry_model_desc(ctypes.Structure):
+    _fields_ = [("in_dim", _c.c_int32), ("hidden", _c.c_int32), ("out_dim", _c.c_int32),
+                ("W1", _p), ("b1", _p), ("W2", _p), ("b2", _p), ("n_hubs", _c.c_int32),
+                ("hub_nodes", _p), ("hub_emb", _p), ("hub_degree", _c.c_int32),
+                ("hub_graph", _p), ("hub_entry", _c.c_int32)]
+
+
+ENTRY_MEDOID, ENTRY_LEARNED_NAV, ENTRY_LEARNED_EXHAUSTIVE = 0, 1, 2
+
+
 class AnnError(RuntimeError):
     def __init__(self, status, where):
         self.status = status
@@ -71,6 +81,22 @@ def load_library(path: str | None = None):
         "ann_medoid": ([_p, i64, i32, i32, _c.POINTER(i32), _p], i32),
         "ann_build_graph": ([_p, i64, i32, i32, i32, i32, _c.c_float, _p, _c.POINTER(i32),
                              _c.POINTER(i64), _p], i32),
+        "ann_set_entry_model": ([_p, _c.POINTER(ann_entry_model_desc), _p], i32),
+        "ann_get_entry_model": ([_p] + [_p] * 7 + [_c.POINTER(i32)], i32),
+        "ann_select_entry": ([_p, _p, i64, i32, i32, _p, _p, _p], i32),
+        "ann_trainer_create": ([i32, i32, i32, _p, _p, _p, _p, _p, i64, _c.c_float, _c.c_float,
+                                _c.c_float, _c.c_float, _c.c_float, pp], i32),
+        "ann_trainer_free": ([_p], i32),
+        "ann_trainer_step": ([_p, _p, _p, i64, _p, i32, _c.POINTER(_c.c_float), _p], i32),
+        "ann_trainer_fit": ([_p, _p, i64, _p, _p, i32, _p, _p], i32),
+        "ann_trainer_get": ([_p, _p, _p, _p, _p, _p, i32], i32),
+        "ann_trainer_attach": ([_p, _p, _p, i32, _p], i32),
+        "ann_adam_update": ([_p, _p, _p, _p, i64, i64, _c.c_float, _c.c_float, _c.c_float,
+                             _c.c_float, _p], i32),
+        "ann_kmeans": ([_p, i64, i32, i32, _p, i64, i32, _p, i32, _p, _p, _p], i32),
+        "ann_assign_hubs": ([_p, i64, i32, i32, _p, i32, _p, _p, _p], i32),
+        "ann_hub_costs": ([_p, _p, i64, _p, _p, i32, _p, i32, i32, _p, _p, _p], i32),
+        "ann_hub_labels": ([_p, _p, _p, i64, i32, i32, i32, i32, _p, _p, _p], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -195,3 +221,111 @@ def ann_build_graph(base, n, dim, dtype, K, R, alpha, graph, medoid=-1, stream=N
                                           ctypes.byref(rep), _stream(stream)),
            "ann_build_graph")
     return m.value, rep.value
+
+
+def ann_set_entry_model(h, in_dim, W1, b1, W2, b2, hub_nodes, hub_emb, hub_degree,
+                        hub_graph=None, hub_entry=-1, stream=None):
+    """Attach the two-tower entry model (arrays: numpy or torch, host or device)."""
+    d = ann_entry_model_desc(in_dim=int(in_dim), hidden=256, out_dim=64, W1=_ptr(W1), b1=_ptr(b1),
+                             W2=_ptr(W2), b2=_ptr(b2), n_hubs=int(len(hub_nodes)),
+                             hub_nodes=_ptr(hub_nodes), hub_emb=_ptr(hub_emb),
+                             hub_degree=int(hub_degree), hub_graph=_ptr(hub_graph),
+                             hub_entry=int(hub_entry))
+    _check(load_library().ann_set_entry_model(h, ctypes.byref(d), _stream(stream)),
+           "ann_set_entry_model")
+
+
+def ann_get_entry_model(h, W1=None, b1=None, W2=None, b2=None, hub_emb=None, hub_nodes=None,
+                        hub_graph=None):
+    """Copy the attached model into the given buffers; returns the entry hub."""
+    e = _c.c_int32(-1)
+    _check(load_library().ann_get_entry_model(h, _ptr(W1), _ptr(b1), _ptr(W2), _ptr(b2),
+                                              _ptr(hub_emb), _ptr(hub_nodes), _ptr(hub_graph),
+                                              ctypes.byref(e)), "ann_get_entry_model")
+    return e.value
+
+
+def ann_select_entry(h, queries, nq, mode, L_hub, entry_out, qhat_out=None, stream=None):
+    """Queue entry selection; node ids land in entry_out (device int32[nq])."""
+    _check(load_library().ann_select_entry(h, _ptr(queries), int(nq), int(mode), int(L_hub),
+                                           _ptr(entry_out), _ptr(qhat_out), _stream(stream)),
+           "ann_select_entry")
+
+
+def ann_trainer_create(in_dim, W1, b1, W2, b2, hub_emb, max_batch, tau=0.07, lr=5e-5,
+                       beta1=0.9, beta2=0.999, eps=1e-8, device=0):
+    h = _p()
+    _check(load_library().ann_trainer_create(int(device), int(in_dim), int(len(hub_emb)),
+                                             _ptr(W1), _ptr(b1), _ptr(W2), _ptr(b2), _ptr(hub_emb),
+                                             int(max_batch), float(tau), float(lr), float(beta1),
+                                             float(beta2), float(eps), ctypes.byref(h)),
+           "ann_trainer_create")
+    return h.value
+
+
+def ann_trainer_free(t):
+    _check(load_library().ann_trainer_free(t), "ann_trainer_free")
+
+
+def ann_trainer_step(t, queries, rows, nb, mask, apply_update=True, stream=None):
+    """One step; returns the batch loss (blocking)."""
+    loss = _c.c_float(0.0)
+    _check(load_library().ann_trainer_step(t, _ptr(queries), _ptr(rows), int(nb), _ptr(mask),
+                                           int(bool(apply_update)), ctypes.byref(loss),
+                                           _stream(stream)), "ann_trainer_step")
+    return loss.value
+
+
+def ann_trainer_fit(t, queries, nt, mask, order, epochs, losses=None, stream=None):
+    _check(load_library().ann_trainer_fit(t, _ptr(queries), int(nt), _ptr(mask), _ptr(order),
+                                          int(epochs), _ptr(losses), _stream(stream)),
+           "ann_trainer_fit")
+
+
+def ann_trainer_get(t, W1=None, b1=None, W2=None, b2=None, hub_emb=None, gradients=False):
+    _check(load_library().ann_trainer_get(t, _ptr(W1), _ptr(b1), _ptr(W2), _ptr(b2),
+                                          _ptr(hub_emb), int(bool(gradients))), "ann_trainer_get")
+
+
+def ann_trainer_attach(t, h, hub_nodes, hub_degree, stream=None):
+    _check(load_library().ann_trainer_attach(t, h, _ptr(hub_nodes), int(hub_degree),
+                                             _stream(stream)), "ann_trainer_attach")
+
+
+def ann_adam_update(params, grads, m, v, n, step, lr, beta1=0.9, beta2=0.999, eps=1e-8,
+                    stream=None):
+    _check(load_library().ann_adam_update(_ptr(params), _ptr(grads), _ptr(m), _ptr(v), int(n),
+                                          int(step), float(lr), float(beta1), float(beta2),
+                                          float(eps), _stream(stream)), "ann_adam_update")
+
+
+def ann_kmeans(x, n, dim, dtype, sample_rows, k, init, iters, centroids, stream=None):
+    """Lloyd's k-means on the sample rows (host int64) from init (host int32);
+    returns the objective per iteration."""
+    import numpy as np
+    sr = np.ascontiguousarray(sample_rows, np.int64)
+    ini = np.ascontiguousarray(init, np.int32)
+    obj = np.zeros(max(1, int(iters)), np.float64)
+    _check(load_library().ann_kmeans(_ptr(x), int(n), int(dim), int(dtype), sr.ctypes.data,
+                                     int(len(sr)), int(k), ini.ctypes.data, int(iters),
+                                     _ptr(centroids), obj.ctypes.data, _stream(stream)),
+           "ann_kmeans")
+    return obj[:iters]
+
+
+def ann_assign_hubs(base, n, dim, dtype, centroids, k, hubs, assign=None, stream=None):
+    _check(load_library().ann_assign_hubs(_ptr(base), int(n), int(dim), int(dtype),
+                                          _ptr(centroids), int(k), _ptr(hubs), _ptr(assign),
+                                          _stream(stream)), "ann_assign_hubs")
+
+
+def ann_hub_costs(h, queries, nq, targets, cand, M, hub_nodes, L, evals, hops, W=1, stream=None):
+    _check(load_library().ann_hub_costs(h, _ptr(queries), int(nq), _ptr(targets), _ptr(cand),
+                                        int(M), _ptr(hub_nodes), int(L), int(W), _ptr(evals),
+                                        _ptr(hops), _stream(stream)), "ann_hub_costs")
+
+
+def ann_hub_labels(evals, hops, cand, nq, M, n_hubs, t_pos, t_neg, mask, best=None, stream=None):
+    _check(load_library().ann_hub_labels(_ptr(evals), _ptr(hops), _ptr(cand), int(nq), int(M),
+                                         int(n_hubs), int(t_pos), int(t_neg), _ptr(mask),
+                                         _ptr(best), _stream(stream)), "ann_hub_labels")

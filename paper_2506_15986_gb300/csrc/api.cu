@@ -9,6 +9,7 @@
 #include <new>
 #include <vector>
 
+#include "entry.h"
 #include "internal.h"
 
 namespace ann {
@@ -83,6 +84,7 @@ void destroy(ann_index *idx)
     cudaFree(idx->d_graph);
     cudaFree(idx->d_base_f32);
     cudaFree(idx->d_status);
+    free_model(idx->model);
     if (idx->pool)
         cudaMemPoolDestroy(idx->pool);
     delete idx;
@@ -252,9 +254,9 @@ ann_status ann_index_info(const ann_index *idx, int64_t *n, int32_t *dim, int32_
     if (medoid)
         *medoid = idx->medoid;
     if (n_hubs)
-        *n_hubs = 0;
+        *n_hubs = idx->model ? idx->model->H : 0;
     if (has_model)
-        *has_model = 0;
+        *has_model = idx->model ? 1 : 0;
     return ANN_OK;
 }
 

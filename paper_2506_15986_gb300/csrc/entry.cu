@@ -1,0 +1,658 @@
+// entry.cu -- learned entry selection (Sec. 4.3) on tcgen05 tensor cores.
+//
+// Query tower (Module II, "lightweight MLP with ReLU"):
+//     q -> Z1 = q W1 + b1 -> A1 = ReLU(Z1) -> Z2 = A1 W2 + b2 -> q_hat = Z2/|Z2|
+// fused in one kernel: 128 queries per CTA, GEMM 1 (K = dim, N = 256) and
+// GEMM 2 (K = 256, N = 64) on kind::f16 MMAs with BF16 operands and FP32
+// accumulators in TMEM; the hidden layer goes TMEM -> registers (bias, ReLU,
+// BF16) -> shared memory -> GEMM 2 without leaving the SM.
+// Hub side: each hub v has an embedding e_v; e_hat_v = e_v / |e_v| is kept as
+// BF16.  The entry of a query is the hub node of argmax_v q_hat . e_hat_v,
+// found either exhaustively (hub_argmax_kernel, a tcgen05 GEMM with a fused
+// per-row argmax epilogue) or by the greedy search of Algorithm 1 with the
+// inner-product metric over the high-tier hub graph (Sec. 4.3: every hub
+// linked to its s most cosine-similar hubs), which reuses the beam-search
+// kernel on a BF16 index of the hub embeddings.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "entry.h"
+#include "internal.h"
+#include "tc.cuh"
+
+namespace ann {
+namespace {
+
+// ---- query tower ------------------------------------------------------------
+
+constexpr int kTowerSmem = 16384 + 32768 + 65536 + 64;
+
+struct TowerArgs {
+    Operand X;  // queries: rows = nq, cols = in_dim
+    const __nv_bfloat16 *W1t;  // [256][in_dim]
+    int in_dim;
+    const float *b1;
+    const __nv_bfloat16 *W2t;  // [64][256]
+    const float *b2;
+    int64_t nq;
+    float *qhat;                // [nq][64] optional
+    __nv_bfloat16 *qhat_bf;     // [nq][64] optional
+    float *z1;                  // [nq][256] optional (training)
+    __nv_bfloat16 *a1;          // [nq][256] optional (training)
+    float *nrm;                 // [nq] optional (training)
+    int *status;
+};
+
+__device__ __forceinline__ uint4 pack8_bf16(const float *a)
+{
+    uint4 o;
+    __nv_bfloat162 h0 = __floats2bfloat162_rn(a[0], a[1]), h1 = __floats2bfloat162_rn(a[2], a[3]);
+    __nv_bfloat162 h2 = __floats2bfloat162_rn(a[4], a[5]), h3 = __floats2bfloat162_rn(a[6], a[7]);
+    o.x = *reinterpret_cast<uint32_t *>(&h0);
+    o.y = *reinterpret_cast<uint32_t *>(&h1);
+    o.z = *reinterpret_cast<uint32_t *>(&h2);
+    o.w = *reinterpret_cast<uint32_t *>(&h3);
+    return o;
+}
+
+__global__ void __launch_bounds__(128) tower_forward_kernel(const TowerArgs t)
+{
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t *sA = smem;            // 128 x 64 canonical (16 KB)
+    uint8_t *sB = smem + 16384;    // 256 x 64 or 64 x 256 canonical (32 KB)
+    uint8_t *sH = smem + 49152;    // 128 x 256 hidden layer, canonical KG=32 (64 KB)
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 114688);
+    uint32_t *slot = reinterpret_cast<uint32_t *>(smem + 114688 + 8);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m = warp * 32 + lane;
+    const int64_t r0 = static_cast<int64_t>(blockIdx.x) * 128;
+    const int64_t row = r0 + m;
+    const bool live = row < t.nq;
+
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    if (warp == 0)
+        tmem_alloc(slot, 256);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *slot;
+    const uint32_t my_lane = tmem + (static_cast<uint32_t>(warp * 32) << 16);
+    uint32_t phase = 0;
+
+    // GEMM 1: [128 x in_dim] x [in_dim x 256]
+    const Operand W1{t.W1t, OP_BF16, t.in_dim, 1, 256, t.in_dim, nullptr};
+    bool ok = tc_gemm_tile<256>(t.X, r0, W1, 0, t.in_dim, sA, sB, bar, phase, tmem);
+    if (ok) {
+        for (int c0 = 0; c0 < 256; c0 += 32) {
+            float v[32];
+            tmem_ld32(my_lane + c0, v);
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                v[j] += t.b1[c0 + j];
+            if (t.z1 && live) {
+                float4 *dst = reinterpret_cast<float4 *>(t.z1 + row * 256 + c0);
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+            }
+#pragma unroll
+            for (int j = 0; j < 32; j += 8) {
+                float a[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    a[u] = fmaxf(v[j + u], 0.f);
+                const uint4 pk = pack8_bf16(a);
+                *reinterpret_cast<uint4 *>(sH + canon_off(m, c0 + j, 32)) = pk;
+                if (t.a1 && live)
+                    *reinterpret_cast<uint4 *>(t.a1 + row * 256 + c0 + j) = pk;
+            }
+        }
+        // GEMM 2: [128 x 256] x [256 x 64]; W2t staged whole (64 rows x 256 k)
+        const Operand W2{t.W2t, OP_BF16, 256, 1, 64, 256, nullptr};
+        stage_tile<64, 32>(sB, W2, 0, 0);
+        fence_proxy_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            tc_fence_after();
+            constexpr uint32_t ID2 = idesc_bf16_f32(128, 64);
+#pragma unroll
+            for (int kk = 0; kk < 16; ++kk)
+                tc_mma(tmem, smem_desc(sH + kk * 256, 128, 4096), smem_desc(sB + kk * 256, 128, 4096), ID2,
+                       kk > 0 ? 1u : 0u);
+            tc_commit(bar);
+        }
+        ok = tc_wait(bar, phase);
+    }
+    if (ok) {
+        float z[64];
+        float v[32];
+        tmem_ld32(my_lane, v);
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+            z[j] = v[j] + t.b2[j];
+        tmem_ld32(my_lane + 32, v);
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+            z[32 + j] = v[j] + t.b2[32 + j];
+        float ss = 0.f;
+#pragma unroll
+        for (int j = 0; j < 64; ++j)
+            ss = fmaf(z[j], z[j], ss);
+        const float nrm = sqrtf(ss);
+        const float inv = nrm > 0.f ? 1.0f / nrm : 0.f;
+        if (live) {
+            if (t.nrm)
+                t.nrm[row] = nrm;
+#pragma unroll
+            for (int j = 0; j < 64; ++j)
+                z[j] *= inv;
+            if (t.qhat) {
+                float4 *dst = reinterpret_cast<float4 *>(t.qhat + row * 64);
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    dst[j] = make_float4(z[4 * j], z[4 * j + 1], z[4 * j + 2], z[4 * j + 3]);
+            }
+            if (t.qhat_bf) {
+                uint4 *dst = reinterpret_cast<uint4 *>(t.qhat_bf + row * 64);
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    dst[j] = pack8_bf16(z + 8 * j);
+            }
+        }
+    } else if (threadIdx.x == 0) {
+        atomicOr(t.status, kStatusTimeoutBit);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 256);
+    }
+}
+
+// ---- exhaustive hub scoring with a fused argmax ------------------------------
+
+// 100 KB keeps at most two CTAs (2 x 256 TMEM columns) on an SM
+constexpr int kArgmaxSmem = 100 * 1024;
+
+__global__ void __launch_bounds__(128)
+    hub_argmax_kernel(const Operand Q, const __nv_bfloat16 *Eb, int H, int64_t nq, const int32_t *hub_nodes,
+                      int32_t *out_node, int32_t *out_hub, float *out_score, int *status)
+{
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t *sA = smem;
+    uint8_t *sB = smem + 16384;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 49152);
+    uint32_t *slot = reinterpret_cast<uint32_t *>(smem + 49152 + 8);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t r0 = static_cast<int64_t>(blockIdx.x) * 128;
+    const int64_t row = r0 + warp * 32 + lane;
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    if (warp == 0)
+        tmem_alloc(slot, 256);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *slot;
+    const uint32_t my_lane = tmem + (static_cast<uint32_t>(warp * 32) << 16);
+    uint32_t phase = 0;
+    const Operand E{Eb, OP_BF16, 64, 1, H, 64, nullptr};
+    float best = -INFINITY;
+    int bi = -1;
+    bool ok = true;
+    for (int c0 = 0; c0 < H && ok; c0 += 256) {
+        ok = tc_gemm_tile<256>(Q, r0, E, c0, 64, sA, sB, bar, phase, tmem);
+        if (!ok)
+            break;
+        for (int cc = 0; cc < 256 && c0 + cc < H; cc += 32) {
+            float v[32];
+            tmem_ld32(my_lane + cc, v);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int col = c0 + cc + j;
+                if (col < H && v[j] > best) {  // strict: the first maximum wins
+                    best = v[j];
+                    bi = col;
+                }
+            }
+        }
+        tc_fence_before();
+    }
+    if (!ok && threadIdx.x == 0)
+        atomicOr(status, kStatusTimeoutBit);
+    if (row < nq) {
+        const bool good = ok && bi >= 0;
+        if (out_hub)
+            out_hub[row] = good ? bi : -1;
+        if (out_score)
+            out_score[row] = good ? best : -INFINITY;
+        if (out_node)
+            out_node[row] = good ? hub_nodes[bi] : -1;
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 256);
+    }
+}
+
+// ---- model preparation ------------------------------------------------------
+
+// BF16 transposed weight copies for K-major B operands, and normalised hub
+// embeddings (FP32 and BF16)
+__global__ void prepare_model_kernel(const float *W1, const float *W2, const float *E, int in_dim, int H,
+                                     __nv_bfloat16 *W1t, __nv_bfloat16 *W2t, float *En, __nv_bfloat16 *Eb)
+{
+    const int64_t tid = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    const int64_t n1 = static_cast<int64_t>(in_dim) * 256, n2 = 256 * 64;
+    if (tid < n1) {
+        const int n = static_cast<int>(tid / in_dim), k = static_cast<int>(tid % in_dim);
+        W1t[tid] = __float2bfloat16_rn(W1[static_cast<int64_t>(k) * 256 + n]);
+    } else if (tid < n1 + n2) {
+        const int64_t i = tid - n1;
+        const int n = static_cast<int>(i / 256), k = static_cast<int>(i % 256);
+        W2t[i] = __float2bfloat16_rn(W2[k * 64 + n]);
+    } else if (tid < n1 + n2 + H) {
+        const int64_t h = tid - n1 - n2;
+        float ss = 0.f;
+        for (int j = 0; j < 64; ++j)
+            ss = fmaf(E[h * 64 + j], E[h * 64 + j], ss);
+        const float inv = ss > 0.f ? rsqrtf(ss) : 0.f;
+        for (int j = 0; j < 64; ++j) {
+            const float v = E[h * 64 + j] * inv;
+            En[h * 64 + j] = v;
+            Eb[h * 64 + j] = __float2bfloat16_rn(v);
+        }
+    }
+}
+
+// hub with the largest cosine to the mean raw embedding (first maximum)
+__global__ void hub_entry_kernel(const float *E, int H, int32_t *out)
+{
+    __shared__ float mean[64];
+    __shared__ float best_v[256];
+    __shared__ int best_i[256];
+    const int t = threadIdx.x;
+    if (t < 64) {
+        float s = 0.f;
+        for (int h = 0; h < H; ++h)
+            s += E[static_cast<int64_t>(h) * 64 + t];
+        mean[t] = s / static_cast<float>(H);
+    }
+    __syncthreads();
+    float mn = 0.f;
+    for (int j = 0; j < 64; ++j)
+        mn = fmaf(mean[j], mean[j], mn);
+    mn = sqrtf(mn);
+    float bv = -INFINITY;
+    int bidx = 0x7fffffff;
+    for (int h = t; h < H; h += blockDim.x) {
+        float dot = 0.f, ee = 0.f;
+        for (int j = 0; j < 64; ++j) {
+            const float e = E[static_cast<int64_t>(h) * 64 + j];
+            dot = fmaf(e, mean[j], dot);
+            ee = fmaf(e, e, ee);
+        }
+        const float c = dot / (sqrtf(ee) * mn);
+        if (c > bv) {
+            bv = c;
+            bidx = h;
+        }
+    }
+    best_v[t] = bv;
+    best_i[t] = bidx;
+    __syncthreads();
+    if (t == 0) {
+        float v = best_v[0];
+        int i = best_i[0];
+        for (int u = 1; u < blockDim.x; ++u)
+            if (best_v[u] > v || (best_v[u] == v && best_i[u] < i)) {
+                v = best_v[u];
+                i = best_i[u];
+            }
+        *out = i;
+    }
+}
+
+__global__ void map_hub_nodes(const int32_t *hub_ids, int64_t nq, int stride, const int32_t *hub_nodes,
+                              int32_t medoid, int32_t *out)
+{
+    const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (i < nq) {
+        const int32_t h = hub_ids[i * stride];
+        out[i] = h >= 0 ? hub_nodes[h] : medoid;
+    }
+}
+
+__global__ void fill_i32(int32_t *p, int64_t n, int32_t v)
+{
+    const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (i < n)
+        p[i] = v;
+}
+
+template <typename T>
+T *dev_alloc(size_t count, cudaError_t &e)
+{
+    T *p = nullptr;
+    if (e == cudaSuccess)
+        e = cudaMalloc(reinterpret_cast<void **>(&p), count * sizeof(T));
+    return p;
+}
+
+}  // namespace
+
+void free_model(ann_entry_model *m)
+{
+    if (!m)
+        return;
+    cudaFree(m->W1);
+    cudaFree(m->b1);
+    cudaFree(m->W2);
+    cudaFree(m->b2);
+    cudaFree(m->E);
+    cudaFree(m->W1t);
+    cudaFree(m->W2t);
+    cudaFree(m->En);
+    cudaFree(m->Eb);
+    cudaFree(m->hub_nodes);
+    cudaFree(m->hub_graph);
+    if (m->hub_index)
+        ann_free_index(m->hub_index);
+    delete m;
+}
+
+ann_status prepare_model(ann_entry_model *m, cudaStream_t s)
+{
+    const int64_t total = static_cast<int64_t>(m->in_dim) * 256 + 256 * 64 + m->H;
+    prepare_model_kernel<<<static_cast<unsigned>((total + 255) / 256), 256, 0, s>>>(
+        m->W1, m->W2, m->E, m->in_dim, m->H, m->W1t, m->W2t, m->En, m->Eb);
+    return cuda_status(cudaGetLastError());
+}
+
+ann_status launch_tower(const ann_entry_model *m, const Operand &X, int64_t nq, float *qhat,
+                        __nv_bfloat16 *qhat_bf, float *z1, __nv_bfloat16 *a1, float *nrm, int *status,
+                        cudaStream_t s)
+{
+    if (nq == 0)
+        return ANN_OK;
+    TowerArgs t{};
+    t.X = X;
+    t.W1t = m->W1t;
+    t.in_dim = m->in_dim;
+    t.b1 = m->b1;
+    t.W2t = m->W2t;
+    t.b2 = m->b2;
+    t.nq = nq;
+    t.qhat = qhat;
+    t.qhat_bf = qhat_bf;
+    t.z1 = z1;
+    t.a1 = a1;
+    t.nrm = nrm;
+    t.status = status;
+    cudaError_t e = cudaFuncSetAttribute(tower_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kTowerSmem);
+    if (e != cudaSuccess)
+        return cuda_status(e);
+    tower_forward_kernel<<<static_cast<unsigned>((nq + 127) / 128), 128, kTowerSmem, s>>>(t);
+    return cuda_status(cudaGetLastError());
+}
+
+ann_status launch_hub_argmax(const ann_entry_model *m, const Operand &Q, int64_t nq, int32_t *out_node,
+                             int32_t *out_hub, float *out_score, int *status, cudaStream_t s)
+{
+    if (nq == 0)
+        return ANN_OK;
+    cudaError_t e = cudaFuncSetAttribute(hub_argmax_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kArgmaxSmem);
+    if (e != cudaSuccess)
+        return cuda_status(e);
+    hub_argmax_kernel<<<static_cast<unsigned>((nq + 127) / 128), 128, kArgmaxSmem, s>>>(
+        Q, m->Eb, m->H, nq, m->hub_nodes, out_node, out_hub, out_score, status);
+    return cuda_status(cudaGetLastError());
+}
+
+ann_status build_hub_index(ann_index *idx, ann_entry_model *m, const int32_t *hub_graph, int32_t hub_entry,
+                           cudaStream_t s)
+{
+    cudaError_t e = cudaSuccess;
+    if (!m->hub_graph)
+        m->hub_graph = dev_alloc<int32_t>(static_cast<size_t>(m->H) * m->s, e);
+    if (e != cudaSuccess)
+        return cuda_status(e);
+    if (hub_graph) {
+        e = cudaMemcpyAsync(m->hub_graph, hub_graph, static_cast<size_t>(m->H) * m->s * 4, cudaMemcpyDefault, s);
+    } else {
+        // the s most cosine-similar other hubs (smaller index on ties)
+        void *dd = nullptr;
+        e = cudaMallocAsync(&dd, static_cast<size_t>(m->H) * m->s * 4, s);
+        if (e == cudaSuccess) {
+            ann_status st = knn_exact(m->En, m->H, 64, ANN_F32, ANN_IP, m->En, m->H, m->s, true, m->hub_graph, dd, s);
+            cudaFreeAsync(dd, s);
+            if (st != ANN_OK)
+                return st;
+        }
+    }
+    if (e != cudaSuccess)
+        return cuda_status(e);
+    if (hub_entry >= 0) {
+        m->hub_entry = hub_entry;
+    } else {
+        int32_t *d = nullptr;
+        e = cudaMallocAsync(reinterpret_cast<void **>(&d), 4, s);
+        if (e == cudaSuccess) {
+            hub_entry_kernel<<<1, 256, 0, s>>>(m->E, m->H, d);
+            e = cudaMemcpyAsync(&m->hub_entry, d, 4, cudaMemcpyDeviceToHost, s);
+            cudaFreeAsync(d, s);
+        }
+        if (e == cudaSuccess)
+            e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess)
+            return cuda_status(e);
+    }
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess)
+        return cuda_status(e);
+    if (m->hub_index) {
+        ann_free_index(m->hub_index);
+        m->hub_index = nullptr;
+    }
+    ann_index_desc d{};
+    d.n = m->H;
+    d.dim = 64;
+    d.degree = m->s;
+    d.dtype = ANN_BF16;
+    d.metric = ANN_IP;
+    d.base = m->Eb;
+    d.graph = m->hub_graph;
+    d.medoid = m->hub_entry;
+    d.base_f32 = nullptr;
+    return ann_index_create(&d, idx->device, &m->hub_index);
+}
+
+}  // namespace ann
+
+using namespace ann;
+
+extern "C" {
+
+ann_status ann_set_entry_model(ann_index *idx, const ann_entry_model_desc *md, void *stream)
+{
+    if (!idx || !md)
+        return ANN_ERR_INVALID_ARG;
+    if (md->in_dim != idx->dim || md->hidden != 256 || md->out_dim != 64 || md->in_dim > 512 ||
+        md->n_hubs < 2 || md->hub_degree < 1 || md->hub_degree > 32 || md->hub_degree >= md->n_hubs ||
+        !md->W1 || !md->b1 || !md->W2 || !md->b2 || !md->hub_nodes || !md->hub_emb ||
+        md->hub_entry >= md->n_hubs)
+        return ANN_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(idx->device);
+    ann_entry_model *m = new (std::nothrow) ann_entry_model();
+    if (!m) {
+        cudaSetDevice(prev);
+        return ANN_ERR_OOM;
+    }
+    m->in_dim = md->in_dim;
+    m->H = md->n_hubs;
+    m->s = md->hub_degree;
+    const int H = m->H;
+    cudaError_t e = cudaSuccess;
+    m->W1 = dev_alloc<float>(static_cast<size_t>(m->in_dim) * 256, e);
+    m->b1 = dev_alloc<float>(256, e);
+    m->W2 = dev_alloc<float>(256 * 64, e);
+    m->b2 = dev_alloc<float>(64, e);
+    m->E = dev_alloc<float>(static_cast<size_t>(H) * 64, e);
+    m->W1t = dev_alloc<__nv_bfloat16>(static_cast<size_t>(m->in_dim) * 256, e);
+    m->W2t = dev_alloc<__nv_bfloat16>(256 * 64, e);
+    m->En = dev_alloc<float>(static_cast<size_t>(H) * 64, e);
+    m->Eb = dev_alloc<__nv_bfloat16>(static_cast<size_t>(H) * 64, e);
+    m->hub_nodes = dev_alloc<int32_t>(H, e);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(m->W1, md->W1, static_cast<size_t>(m->in_dim) * 256 * 4, cudaMemcpyDefault, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(m->b1, md->b1, 256 * 4, cudaMemcpyDefault, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(m->W2, md->W2, 256 * 64 * 4, cudaMemcpyDefault, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(m->b2, md->b2, 64 * 4, cudaMemcpyDefault, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(m->E, md->hub_emb, static_cast<size_t>(H) * 64 * 4, cudaMemcpyDefault, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(m->hub_nodes, md->hub_nodes, static_cast<size_t>(H) * 4, cudaMemcpyDefault, s);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(s);
+    ann_status st = cuda_status(e);
+    if (st == ANN_OK) {
+        // hub node ids must be valid nodes
+        std::vector<int32_t> hn(H);
+        st = cuda_status(cudaMemcpy(hn.data(), m->hub_nodes, static_cast<size_t>(H) * 4, cudaMemcpyDeviceToHost));
+        for (int i = 0; st == ANN_OK && i < H; ++i)
+            if (hn[i] < 0 || hn[i] >= idx->n)
+                st = ANN_ERR_INVALID_ARG;
+    }
+    if (st == ANN_OK)
+        st = prepare_model(m, s);
+    if (st == ANN_OK)
+        st = build_hub_index(idx, m, md->hub_graph, md->hub_entry, s);
+    if (st != ANN_OK) {
+        free_model(m);
+        cudaSetDevice(prev);
+        return st;
+    }
+    free_model(idx->model);
+    idx->model = m;
+    cudaSetDevice(prev);
+    return ANN_OK;
+}
+
+ann_status ann_get_entry_model(const ann_index *idx, float *W1, float *b1, float *W2, float *b2, float *hub_emb,
+                               int32_t *hub_nodes, int32_t *hub_graph, int32_t *hub_entry)
+{
+    if (!idx || !idx->model)
+        return ANN_ERR_INVALID_ARG;
+    const ann_entry_model *m = idx->model;
+    cudaError_t e = cudaSuccess;
+    auto cp = [&](void *dst, const void *src, size_t bytes) {
+        if (dst && e == cudaSuccess)
+            e = cudaMemcpy(dst, src, bytes, cudaMemcpyDefault);
+    };
+    cp(W1, m->W1, static_cast<size_t>(m->in_dim) * 256 * 4);
+    cp(b1, m->b1, 256 * 4);
+    cp(W2, m->W2, 256 * 64 * 4);
+    cp(b2, m->b2, 64 * 4);
+    cp(hub_emb, m->E, static_cast<size_t>(m->H) * 64 * 4);
+    cp(hub_nodes, m->hub_nodes, static_cast<size_t>(m->H) * 4);
+    cp(hub_graph, m->hub_graph, static_cast<size_t>(m->H) * m->s * 4);
+    if (hub_entry)
+        *hub_entry = m->hub_entry;
+    return cuda_status(e);
+}
+
+ann_status ann_select_entry(ann_index *idx, const void *d_queries, int64_t nq, int32_t mode, int32_t L_hub,
+                            int32_t *d_entry, float *d_qhat, void *stream)
+{
+    if (!idx || nq < 0 || (mode != ANN_ENTRY_MEDOID && mode != ANN_ENTRY_LEARNED_NAV &&
+                           mode != ANN_ENTRY_LEARNED_EXHAUSTIVE))
+        return ANN_ERR_INVALID_ARG;
+    if (nq == 0)
+        return ANN_OK;
+    if (!d_entry || !d_queries || (reinterpret_cast<uintptr_t>(d_queries) & 15) ||
+        (reinterpret_cast<uintptr_t>(d_qhat) & 15))
+        return ANN_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(idx->device);
+    ann_status st = ANN_OK;
+    if (mode == ANN_ENTRY_MEDOID) {
+        fill_i32<<<static_cast<unsigned>((nq + 255) / 256), 256, 0, s>>>(d_entry, nq, idx->medoid);
+        st = cuda_status(cudaGetLastError());
+        cudaSetDevice(prev);
+        return st;
+    }
+    ann_entry_model *m = idx->model;
+    if (!m || (mode == ANN_ENTRY_LEARNED_NAV && (L_hub < 1 || L_hub > ANN_MAX_L))) {
+        cudaSetDevice(prev);
+        return m ? ANN_ERR_INVALID_ARG : ANN_ERR_UNSUPPORTED;
+    }
+    // scratch: q_hat fp32 + bf16, hub ids, hub scores
+    const size_t qf = static_cast<size_t>(nq) * 64 * 4, qb = static_cast<size_t>(nq) * 64 * 2;
+    const size_t hb = static_cast<size_t>(nq) * 4;
+    void *scr = nullptr;
+    st = scratch_alloc(idx, qf + qb + 2 * hb + 256, s, &scr);
+    if (st != ANN_OK) {
+        cudaSetDevice(prev);
+        return st;
+    }
+    float *qhat = d_qhat ? d_qhat : static_cast<float *>(scr);
+    __nv_bfloat16 *qbf = reinterpret_cast<__nv_bfloat16 *>(static_cast<uint8_t *>(scr) + qf);
+    int32_t *hid = reinterpret_cast<int32_t *>(static_cast<uint8_t *>(scr) + qf + qb);
+    float *hsc = reinterpret_cast<float *>(static_cast<uint8_t *>(scr) + qf + qb + hb);
+    const Operand X{d_queries, idx->dtype == ANN_U8 ? OP_U8 : OP_F32, idx->dim, 1, nq, idx->dim, nullptr};
+    st = launch_tower(m, X, nq, qhat, qbf, nullptr, nullptr, nullptr, idx->d_status, s);
+    if (st == ANN_OK && mode == ANN_ENTRY_LEARNED_EXHAUSTIVE) {
+        const Operand Q{qbf, OP_BF16, 64, 1, nq, 64, nullptr};
+        st = launch_hub_argmax(m, Q, nq, d_entry, hid, hsc, idx->d_status, s);
+    } else if (st == ANN_OK) {
+        ann_search_params p{};
+        p.k = 1;
+        p.L = L_hub;
+        p.W = 1;
+        SearchLaunch Ls{};
+        Ls.queries = qhat;
+        Ls.qbytes = 64 * 4;
+        Ls.nq = nq;
+        Ls.entries = nullptr;
+        Ls.p = &p;
+        Ls.ids = hid;
+        Ls.dists = hsc;
+        Ls.stats = nullptr;
+        st = launch_search(m->hub_index, Ls, s);
+        if (st == ANN_OK) {
+            map_hub_nodes<<<static_cast<unsigned>((nq + 255) / 256), 256, 0, s>>>(hid, nq, 1, m->hub_nodes,
+                                                                                  idx->medoid, d_entry);
+            st = cuda_status(cudaGetLastError());
+        }
+    }
+    scratch_free(idx, scr, s);
+    cudaSetDevice(prev);
+    return st;
+}
+
+}  // extern "C"

@@ -55,6 +55,7 @@ struct SearchLaunch {
     void *scratch;
     size_t scratch_bytes;
     int max_teams;  // cap on the persistent grid (0 = occupancy-limited only)
+    int64_t qdiv;   // work item i uses query row and target i / qdiv (0 = 1)
 };
 
 // Queues the beam-search kernel (search.cu).
@@ -62,5 +63,9 @@ ann_status launch_search(ann_index *idx, const SearchLaunch &L, cudaStream_t s);
 
 // Scratch bytes launch_search needs for `teams` teams at the given params.
 size_t search_scratch_bytes(int teams, int spill_bits);
+
+// Exact k-NN (build.cu): candidates from an fp32 GEMM, exact re-scoring.
+ann_status knn_exact(const void *d_base, int64_t n, int dim, int dtype, int metric, const void *d_queries,
+                     int64_t nq, int k, bool exclude_self, int32_t *d_ids, void *d_dists, cudaStream_t s);
 
 }  // namespace ann

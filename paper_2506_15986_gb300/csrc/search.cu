@@ -44,6 +44,7 @@ struct SearchArgs {
     const uint8_t *queries;
     int qbytes;
     int64_t nq;
+    int64_t qdiv;  // work item i reads query row and target i / qdiv
     const int32_t *entries;
     int32_t medoid;
     int L, k, W;
@@ -217,7 +218,8 @@ __global__ void __launch_bounds__(32 * kSearchWarps) beam_search_kernel(const Se
 
         const int Lq = a.dL ? a.dL[qi] : a.L;
         const int kq = a.dk ? a.dk[qi] : a.k;
-        const int32_t target = a.dtarget ? a.dtarget[qi] : -1;
+        const int64_t qrow = qi / a.qdiv;
+        const int32_t target = a.dtarget ? a.dtarget[qrow] : -1;
         const int32_t entry = a.entries ? a.entries[qi] : a.medoid;
         bool failed = false;
         bool timed_out = false;
@@ -231,7 +233,7 @@ __global__ void __launch_bounds__(32 * kSearchWarps) beam_search_kernel(const Se
         bool gmode = false, found = false;
         if (!failed) {
             // query row -> shared memory; clear the visited table
-            const uint8_t *qsrc = a.queries + qi * a.qbytes;
+            const uint8_t *qsrc = a.queries + qrow * a.qbytes;
             for (int o = lane * 16; o < a.qbytes; o += 32 * 16)
                 *reinterpret_cast<uint4 *>(qbuf + o) = *reinterpret_cast<const uint4 *>(qsrc + o);
             for (int o = lane; o < hcap / 4; o += 32)
@@ -485,6 +487,7 @@ ann_status launch_search(ann_index *idx, const SearchLaunch &L, cudaStream_t s)
     a.queries = static_cast<const uint8_t *>(L.queries);
     a.qbytes = L.qbytes;
     a.nq = L.nq;
+    a.qdiv = L.qdiv > 0 ? L.qdiv : 1;
     a.entries = L.entries;
     a.medoid = idx->medoid;
     a.L = p->L;

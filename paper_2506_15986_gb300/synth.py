@@ -11,12 +11,12 @@ Workloads (default sizes; tests pass smaller ones):
   small_u8     10,000 x 128 uint8, 50 isotropic components, centres U[32,224],
                sigma 20, round-half-even and clip to [0,255]; 100 queries from
                the same mixture.
-  shift_f32    1,000,000 x 128 fp32, 1,000 components with centres
-               N(0, 0.75^2 I) and per-dimension scales LogNormal(0, 0.5) (the
-               centre spread makes components overlap enough that a graph
-               built from exact 64-NN stays navigable, as on real
-               descriptors, while search from one fixed entry still needs a
-               large pool); queries from the
+  shift_f32    1,000,000 x 128 fp32, 1,000 components; dimension i carries a
+               global scale g_i = (1+i)^-0.5 (descriptor-like data have a low
+               intrinsic dimension; with independent equal-variance
+               dimensions, RNG-pruned k-NN graphs in 128-d fragment into many
+               unreachable nodes), centres g * N(0, I) and per-dimension
+               scales g * LogNormal(0, 0.5); queries from the
                same centres moved by a per-component shift N(0, (0.5 sigma)^2)
                and reweighted so that 5% of the components carry 80% of the
                queries; 10,000 evaluation + 100,000 training queries.
@@ -63,10 +63,14 @@ def small_u8(n=10_000, nq=100, d=128, n_comp=50, seed=SEED_BASE + 1):
 
 
 def shift_f32(n=1_000_000, nq=10_000, n_train=100_000, d=128, n_comp=1000,
-              hot_frac=0.05, hot_mass=0.8, centre_scale=0.75, seed=SEED_BASE + 2):
+              hot_frac=0.05, hot_mass=0.8, centre_scale=1.0, spectrum=0.5,
+              seed=SEED_BASE + 2):
     rng = _rng(seed)
-    centres = rng.normal(0.0, centre_scale, size=(n_comp, d)).astype(np.float32)
-    scales = rng.lognormal(0.0, 0.5, size=(n_comp, d)).astype(np.float32)
+    # global variance spectrum: dimension i has scale (1 + i)^-spectrum, which
+    # gives descriptor-like data a low intrinsic dimension (about 18 for 0.5)
+    g = (1.0 + np.arange(d)) ** (-spectrum)
+    centres = (rng.normal(0.0, centre_scale, size=(n_comp, d)) * g).astype(np.float32)
+    scales = (rng.lognormal(0.0, 0.5, size=(n_comp, d)) * g).astype(np.float32)
     shifts = (rng.standard_normal((n_comp, d)) * 0.5 * scales).astype(np.float32)
     n_hot = max(1, int(round(hot_frac * n_comp)))
     hot = rng.permutation(n_comp)[:n_hot]
@@ -177,3 +181,15 @@ def train_batches(n_train, batch, epochs, seed):
     """Per-epoch random permutations of the training queries."""
     rng = _rng(seed)
     return [rng.permutation(n_train).astype(np.int32) for _ in range(epochs)]
+
+
+def model_init(in_dim, n_hubs, hidden=256, out=64, seed=SEED_BASE + 100):
+    """Initial two-tower parameters: He-normal W1, W2 (zero biases) and
+    standard-normal hub embeddings."""
+    rng = _rng(seed)
+    W1 = (rng.standard_normal((in_dim, hidden)) * np.sqrt(2.0 / in_dim)).astype(np.float32)
+    b1 = np.zeros(hidden, np.float32)
+    W2 = (rng.standard_normal((hidden, out)) * np.sqrt(2.0 / hidden)).astype(np.float32)
+    b2 = np.zeros(out, np.float32)
+    E = rng.standard_normal((n_hubs, out)).astype(np.float32)
+    return W1, b1, W2, b2, E

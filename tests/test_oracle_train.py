@@ -124,3 +124,14 @@ def test_hub_argmax_first_maximum():
     Eh = np.array([[0.5, 0.5], [1.0, 0.0], [1.0, 0.0], [0.0, 1.0]])
     arg, s = ot.hub_scores_argmax(Qh, Eh)
     assert arg.tolist() == [1, 3] and s.tolist() == [1.0, 1.0]
+
+
+def test_bf16_round_ties_and_values():
+    # 1 + 2^-8 lies halfway between bf16 neighbours 1 and 1 + 2^-7: ties to even (1)
+    x = np.array([1.0, 1.0 + 2**-8, 1.0 + 3 * 2**-8, -2.5, 3.0e38], np.float32)
+    r = ot.bf16_round(x)
+    assert r[0] == 1.0 and r[1] == 1.0 and r[2] == 1.0 + 2**-6 and r[3] == -2.5
+    # torch's own bfloat16 conversion (round to nearest even) agrees
+    v = np.random.default_rng(0).standard_normal(1000).astype(np.float32)
+    t = torch.from_numpy(v).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(ot.bf16_round(v), t)

@@ -1,0 +1,103 @@
+"""GPU training kernels against the float64 oracle (Sec. 4.3 Eq. loss, Adam).
+
+Tolerance: every GEMM of a step takes BF16 operands (about 2^-9 relative
+rounding each) with FP32 accumulation, and the backward pass chains up to
+four such GEMMs, so each parameter's gradient is compared by its relative
+Frobenius error (<= 3e-2) and cosine (>= 0.999) against the oracle fed the
+same BF16-rounded inputs; the loss within 2e-3 relative.  Adam is elementwise
+fp32 against float64: 1e-5 relative."""
+import numpy as np
+import pytest
+
+from oracle import train as ot
+from paper_2506_15986_gb300 import ann
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+DEV = torch.device("cuda:0")
+
+
+def _problem(B=700, D=128, H=200, seed=0):
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((B + 50, D)).astype(np.float32)
+    W1 = (rng.standard_normal((D, 256)) / np.sqrt(D)).astype(np.float32)
+    b1 = (0.1 * rng.standard_normal(256)).astype(np.float32)
+    W2 = (rng.standard_normal((256, 64)) / 16).astype(np.float32)
+    b2 = (0.1 * rng.standard_normal(64)).astype(np.float32)
+    E = rng.standard_normal((H, 64)).astype(np.float32)
+    mask = rng.choice(np.array([-1, 0, 1], np.int8), size=(B + 50, H), p=[0.6, 0.3, 0.1])
+    mask[3] = 0  # a query without labels
+    rows = rng.permutation(B + 50)[:B].astype(np.int32)  # a batch drawn through a row map
+    return X, W1, b1, W2, b2, E, mask, rows
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def _cos(a, b):
+    return float((a * b).sum() / (np.linalg.norm(a) * np.linalg.norm(b)))
+
+
+def test_gradients_match_oracle():
+    X, W1, b1, W2, b2, E, mask, rows = _problem()
+    tau = 0.1
+    t = ann.ann_trainer_create(128, W1, b1, W2, b2, E, 1024, tau=tau, lr=1e-3)
+    try:
+        dX = torch.from_numpy(X).to(DEV)
+        dm = torch.from_numpy(mask).to(DEV)
+        dr = torch.from_numpy(rows).to(DEV)
+        loss = ann.ann_trainer_step(t, dX, dr, len(rows), dm, apply_update=False)
+        g = {k: np.zeros_like(v) for k, v in dict(W1=W1, b1=b1, W2=W2, b2=b2, E=E).items()}
+        ann.ann_trainer_get(t, g["W1"], g["b1"], g["W2"], g["b2"], g["E"], gradients=True)
+    finally:
+        ann.ann_trainer_free(t)
+    bf = ot.bf16_round
+    ref_loss, ref = ot.loss_and_grads(bf(X[rows]), bf(W1), b1.astype(np.float64), bf(W2),
+                                      b2.astype(np.float64), E.astype(np.float64), mask[rows], tau)
+    assert abs(loss - ref_loss) <= 2e-3 * abs(ref_loss)
+    for k in ("W1", "b1", "W2", "b2", "E"):
+        assert _rel(g[k], ref[k]) <= 3e-2, (k, _rel(g[k], ref[k]))
+        assert _cos(g[k], ref[k]) >= 0.999, (k, _cos(g[k], ref[k]))
+
+
+def test_adam_update_matches_oracle():
+    rng = np.random.default_rng(3)
+    n = 5000
+    p = rng.standard_normal(n).astype(np.float32)
+    m = np.zeros(n, np.float32)
+    v = np.zeros(n, np.float32)
+    dp, dm, dv = (torch.from_numpy(a.copy()).to(DEV) for a in (p, m, v))
+    pr, mr, vr = p.astype(np.float64), m.astype(np.float64), v.astype(np.float64)
+    for step in range(1, 4):
+        gr = rng.standard_normal(n).astype(np.float32)
+        ann.ann_adam_update(dp, torch.from_numpy(gr).to(DEV), dm, dv, n, step, 1e-2)
+        pr, mr, vr = ot.adam_step(pr, gr.astype(np.float64), mr, vr, step, 1e-2)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(dp.cpu().numpy(), pr, rtol=1e-5, atol=1e-6)
+    np.testing.assert_allclose(dm.cpu().numpy(), mr, rtol=1e-5, atol=1e-7)
+
+
+def test_training_lowers_the_loss_and_attaches():
+    X, W1, b1, W2, b2, E, mask, rows = _problem(B=2000, H=64, seed=1)
+    # learnable structure: the positive hub of a query is decided by its first coordinates
+    lab = (np.abs(X[:, :6]).argmax(1) * 10 + (X[:, 6] > 0)).astype(np.int64) % 64
+    mask = np.full((len(X), 64), -1, np.int8)
+    mask[np.arange(len(X)), lab] = 1
+    t = ann.ann_trainer_create(128, W1, b1, W2, b2, E, 512, tau=0.1, lr=3e-3)
+    try:
+        dX = torch.from_numpy(X).to(DEV)
+        dm = torch.from_numpy(mask).to(DEV)
+        nt = len(X)
+        steps = (nt + 511) // 512
+        losses = torch.zeros(30 * steps, device=DEV)
+        ann.ann_trainer_fit(t, dX, nt, dm, None, 30, losses)
+        ls = losses.cpu().numpy()
+        assert ls[-steps:].mean() < 0.5 * ls[:steps].mean()
+        W = np.zeros_like(W1)
+        ann.ann_trainer_get(t, W1=W)
+        assert np.isfinite(W).all() and not np.array_equal(W, W1)
+    finally:
+        ann.ann_trainer_free(t)
