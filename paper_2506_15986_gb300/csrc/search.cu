@@ -503,9 +503,11 @@ ann_status launch_search(ann_index *idx, const SearchLaunch &L, cudaStream_t s)
 
     int hb = p->hash_bits;
     if (hb == 0) {
-        // about 24 evaluations per pool slot fit below the 3/4 load limit
+        // searches evaluate about 10-16 nodes per pool slot; size the shared
+        // table for 16 per slot below its 3/4 load limit (the exact global
+        // spill table takes any excess)
         hb = 10;
-        while ((1 << hb) * 3 / 4 < 24 * p->L && hb < 13)
+        while ((1 << hb) * 3 / 4 < 16 * p->L && hb < 13)
             ++hb;
     }
     a.hash_bits = hb;
@@ -516,9 +518,11 @@ ann_status launch_search(ann_index *idx, const SearchLaunch &L, cudaStream_t s)
     if ((s16 & 1) == 0)
         s16 += 1;  // odd 16-byte stride: 8-lane phases of 16-byte loads hit distinct banks
     a.stage_stride = s16 * 16;
-    // at most 32 rows and 48 KB staged at once (also keeps one mbarrier
-    // phase's byte count far below its 2^20 limit)
-    a.stage_rows = std::max(1, std::min({maxc, 32, 49152 / a.stage_stride}));
+    // Most steps find far fewer new neighbours than W * R (about 9 of 32 on
+    // average), so 16 rows per gather round keep shared memory per team small
+    // (more teams per SM); at most 48 KB staged at once, which also keeps one
+    // mbarrier phase's byte count far below its 2^20 limit.
+    a.stage_rows = std::max(1, std::min({maxc, 16, 49152 / a.stage_stride}));
 
     size_t off = 16;  // mbarrier
     a.off_sel = static_cast<int>(off);
