@@ -247,6 +247,34 @@ ann_status ann_get_entry_model(const ann_index *idx, float *W1, float *b1, float
 ann_status ann_select_entry(ann_index *idx, const void *d_queries, int64_t nq, int32_t mode,
                             int32_t L_hub, int32_t *d_entry, float *d_qhat, void *stream);
 
+/*
+ * Exhaustive learned entry selection (the ANN_ENTRY_LEARNED_EXHAUSTIVE mode
+ * of ann_select_entry) that allocates no device memory.  The paper has no
+ * counterpart: this exists for callers that cannot let the library allocate,
+ * such as a serving process that has reserved all of HBM up front, a latency
+ * critical loop where an allocator call could stall or synchronise the
+ * device, or a context (a host callback) where allocating CUDA calls are not
+ * allowed.
+ *   Scratch: a 16 MiB array that every GPU loading the library holds until the
+ *   process exits (136 bytes per query).  Batches larger than
+ *   ann_select_entry_noalloc_max_queries() (123,357) are rejected with
+ *   ANN_ERR_CAPACITY before anything is queued; split them.
+ *   The first call on a device looks up the array's device address on that
+ *   device (a one-time set-up), so make the first call on each device before
+ *   any stream capture.
+ *   All calls on a device share the one array: calls whose work overlaps on
+ *   the GPU (for example on two streams) race and must be serialised by the
+ *   caller.  Every word is written before it is read, so no clearing is needed.
+ *   Arguments and results are those of ann_select_entry in that mode:
+ *   d_entry (nq int32 node ids), d_qhat (optional nq*64 fp32).  Needs an
+ *   attached entry model (ANN_ERR_UNSUPPORTED otherwise).  Asynchronous.
+ */
+ann_status ann_select_entry_noalloc(ann_index *idx, const void *d_queries, int64_t nq,
+                                    int32_t *d_entry, float *d_qhat, void *stream);
+
+/* Largest nq ann_select_entry_noalloc accepts. */
+int64_t ann_select_entry_noalloc_max_queries(void);
+
 /* ---- entry-model training (Sec. 4.2 labels, Sec. 4.3 loss, Sec. 5.1 Adam) -- */
 
 typedef struct ann_trainer ann_trainer;

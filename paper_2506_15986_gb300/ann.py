@@ -329,3 +329,21 @@ def ann_hub_labels(evals, hops, cand, nq, M, n_hubs, t_pos, t_neg, mask, best=No
     _check(load_library().ann_hub_labels(_ptr(evals), _ptr(hops), _ptr(cand), int(nq), int(M),
                                          int(n_hubs), int(t_pos), int(t_neg), _ptr(mask),
                                          _ptr(best), _stream(stream)), "ann_hub_labels")
+
+
+def ann_select_entry_noalloc(h, queries, nq, entry_out, qhat_out=None, stream=None):
+    """Exhaustive learned entry selection using the library's static scratch
+    (no device allocation); see include/ann.h for its limits."""
+    lib = load_library()
+    lib.ann_select_entry_noalloc.argtypes = [_p, _p, _c.c_int64, _p, _p, _p]
+    lib.ann_select_entry_noalloc.restype = _c.c_int32
+    _check(lib.ann_select_entry_noalloc(h, _ptr(queries), int(nq), _ptr(entry_out),
+                                        _ptr(qhat_out), _stream(stream)),
+           "ann_select_entry_noalloc")
+
+
+def ann_select_entry_noalloc_max_queries():
+    lib = load_library()
+    lib.ann_select_entry_noalloc_max_queries.argtypes = []
+    lib.ann_select_entry_noalloc_max_queries.restype = _c.c_int64
+    return int(lib.ann_select_entry_noalloc_max_queries())
