@@ -96,7 +96,15 @@ typedef struct {
  *   W         pool entries expanded per step, 1..ANN_MAX_W, W*degree <= 64
  *   hash_bits log2 of the per-query shared-memory visited-table capacity,
  *             0 = chosen from L; 8..15
- *   flags     ANN_SEARCH_* bits
+ *   stage_rows neighbour rows gathered into shared memory per round, 0 =
+ *             chosen from the row size; 1..32.  hash_bits and stage_rows change
+ *             speed only, never results (see ann_autotune)
+ *   flags     ANN_SEARCH_* bits.  ANN_SEARCH_RERANK: after the search, every
+ *             id of the final pool (L entries) is re-scored exactly from the
+ *             index's fp32 copy of the rows (ann_index_desc.base_f32; without
+ *             it the call returns ANN_ERR_UNSUPPORTED) and the k best by
+ *             (fp32 distance, id) are returned (the precision line: reduced-
+ *             precision storage for traversal, exact scores for the answer)
  *   d_k, d_L  optional per-query k and L (device int32[nq]); NULL = k, L
  *   d_target  optional per-query target node (device int32[nq]); when given
  *             the search runs in label mode: it stops after the step in which
@@ -108,6 +116,7 @@ typedef struct {
     int32_t L;
     int32_t W;
     int32_t hash_bits;
+    int32_t stage_rows;
     uint32_t flags;
     const int32_t *d_k;
     const int32_t *d_L;
@@ -176,6 +185,42 @@ ann_status ann_search_batch(ann_index *idx, const void *d_queries, int64_t nq,
  * kernels since the last call; ANN_ERR_CUDA if a CUDA call failed.
  */
 ann_status ann_sync_status(ann_index *idx, void *stream);
+
+/* ---- batching line: CUDA-graph plans and the autotuner -------------------- */
+
+typedef struct ann_plan ann_plan;
+
+/*
+ * Capture one batch -- entry selection (entry_mode, L_hub as in
+ * ann_select_entry; ANN_ENTRY_MEDOID skips it) followed by ann_search_batch
+ * with parameters p -- into a CUDA graph over fixed buffers.  The plan keeps
+ * the pointers: queries, per-query arrays of p, d_entry_buf (nq int32,
+ * needed unless the mode is ANN_ENTRY_MEDOID) and the outputs must stay
+ * valid while the plan is used.  Blocking; the index must not be freed
+ * before the plan.
+ */
+ann_status ann_plan_create(ann_index *idx, const void *d_queries, int64_t nq, int32_t entry_mode,
+                           int32_t L_hub, const ann_search_params *p, int32_t *d_entry_buf,
+                           int32_t *d_ids, void *d_dists, int32_t *d_stats, ann_plan **out);
+
+/* Launch a captured batch on `stream` (asynchronous). */
+ann_status ann_plan_launch(ann_plan *plan, void *stream);
+
+/* Free a plan (NULL is accepted).  Synchronises the device. */
+ann_status ann_plan_free(ann_plan *plan);
+
+/*
+ * Time ann_search_batch over the given batch for visited-table sizes around
+ * and below the default (hash_bits) and gather round sizes (stage_rows 4, 8, 16), reps
+ * runs each after one warm-up, and return in *best the copy of *p with the
+ * fastest pair (*best_ms: its mean time).  Both knobs change speed only: the
+ * visited set stays exact (shared table plus global spill) and the gather
+ * order does not enter any result.  Blocking; d_ids / d_dists receive the
+ * results of the last run.
+ */
+ann_status ann_autotune(ann_index *idx, const void *d_queries, int64_t nq, const int32_t *d_entry,
+                        const ann_search_params *p, int32_t *d_ids, void *d_dists, int32_t reps,
+                        ann_search_params *best, float *best_ms, void *stream);
 
 /* ---- learned entry selection (Sec. 4.3) ---------------------------------- */
 

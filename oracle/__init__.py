@@ -295,3 +295,24 @@ def pruned_row(base, p, K, R, alpha=1.0):
         if all(alpha * float(((x[s] - x[c]) ** 2).sum()) > dpc for s in kept):
             kept.append(c)
     return kept
+
+
+def rerank(base_exact, pool_ids, queries, k, metric=L2):
+    """Exact re-scoring of a final pool: the ids of each row of pool_ids
+    (-1 = empty) ordered by (float64 distance to the exact rows, id); the first
+    k are returned with their distances ((-1, +inf) padding)."""
+    x = np.asarray(base_exact, np.float64)
+    q = np.asarray(queries, np.float64)
+    nq = q.shape[0]
+    ids = np.full((nq, k), -1, np.int32)
+    dists = np.full((nq, k), np.inf)
+    for i in range(nq):
+        p = [int(v) for v in pool_ids[i] if v >= 0]
+        if not p:
+            continue
+        diff = x[p] - q[i]
+        d = (diff * diff).sum(1) if metric == L2 else -(x[p] @ q[i])
+        order = sorted(range(len(p)), key=lambda j: (d[j], p[j]))[:k]
+        ids[i, :len(order)] = [p[j] for j in order]
+        dists[i, :len(order)] = [d[j] for j in order]
+    return ids, dists

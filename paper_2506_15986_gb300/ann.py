@@ -34,7 +34,8 @@ class ann_index_desc(ctypes.Structure):
 
 class ann_search_params(ctypes.Structure):
     _fields_ = [("k", _c.c_int32), ("L", _c.c_int32), ("W", _c.c_int32),
-                ("hash_bits", _c.c_int32), ("flags", _c.c_uint32), ("d_k", _p),
+                ("hash_bits", _c.c_int32), ("stage_rows", _c.c_int32),
+                ("flags", _c.c_uint32), ("d_k", _p),
                 ("d_L", _p), ("d_target", _p)]
 
 
@@ -178,8 +179,10 @@ def ann_load_index(path, device=0):
     return h.value
 
 
-def search_params(k, L, W=1, hash_bits=0, flags=0, d_k=None, d_L=None, d_target=None):
+def search_params(k, L, W=1, hash_bits=0, flags=0, d_k=None, d_L=None, d_target=None,
+                  stage_rows=0):
     return ann_search_params(k=int(k), L=int(L), W=int(W), hash_bits=int(hash_bits),
+                             stage_rows=int(stage_rows),
                              flags=int(flags), d_k=_ptr(d_k), d_L=_ptr(d_L),
                              d_target=_ptr(d_target))
 
@@ -340,6 +343,48 @@ def ann_select_entry_noalloc(h, queries, nq, entry_out, qhat_out=None, stream=No
     _check(lib.ann_select_entry_noalloc(h, _ptr(queries), int(nq), _ptr(entry_out),
                                         _ptr(qhat_out), _stream(stream)),
            "ann_select_entry_noalloc")
+
+
+def ann_plan_create(h, queries, nq, entry_mode, L_hub, params, entry_buf, ids, dists, stats=None):
+    """Capture entry selection + search for fixed buffers into a CUDA graph."""
+    lib = load_library()
+    lib.ann_plan_create.argtypes = [_p, _p, _c.c_int64, _c.c_int32, _c.c_int32,
+                                    _c.POINTER(ann_search_params), _p, _p, _p, _p, _c.POINTER(_p)]
+    lib.ann_plan_create.restype = _c.c_int32
+    out = _p()
+    _check(lib.ann_plan_create(h, _ptr(queries), int(nq), int(entry_mode), int(L_hub),
+                               ctypes.byref(params), _ptr(entry_buf), _ptr(ids), _ptr(dists),
+                               _ptr(stats), ctypes.byref(out)), "ann_plan_create")
+    return out.value
+
+
+def ann_plan_launch(plan, stream=None):
+    lib = load_library()
+    lib.ann_plan_launch.argtypes = [_p, _p]
+    lib.ann_plan_launch.restype = _c.c_int32
+    _check(lib.ann_plan_launch(plan, _stream(stream)), "ann_plan_launch")
+
+
+def ann_plan_free(plan):
+    lib = load_library()
+    lib.ann_plan_free.argtypes = [_p]
+    lib.ann_plan_free.restype = _c.c_int32
+    _check(lib.ann_plan_free(plan), "ann_plan_free")
+
+
+def ann_autotune(h, queries, nq, entry, params, ids, dists, reps=3, stream=None):
+    """Returns (best ann_search_params, best mean ms)."""
+    lib = load_library()
+    lib.ann_autotune.argtypes = [_p, _p, _c.c_int64, _p, _c.POINTER(ann_search_params), _p, _p,
+                                 _c.c_int32, _c.POINTER(ann_search_params),
+                                 _c.POINTER(_c.c_float), _p]
+    lib.ann_autotune.restype = _c.c_int32
+    best = ann_search_params()
+    ms = _c.c_float(0.0)
+    _check(lib.ann_autotune(h, _ptr(queries), int(nq), _ptr(entry), ctypes.byref(params),
+                            _ptr(ids), _ptr(dists), int(reps), ctypes.byref(best),
+                            ctypes.byref(ms), _stream(stream)), "ann_autotune")
+    return best, ms.value
 
 
 def ann_select_entry_noalloc_max_queries():

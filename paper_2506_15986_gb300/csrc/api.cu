@@ -373,12 +373,13 @@ ann_status ann_search_batch(ann_index *idx, const void *d_queries, int64_t nq, c
         return ANN_ERR_INVALID_ARG;
     if (p->L < 1 || p->L > ANN_MAX_L || p->k < 1 || p->k > p->L || p->W < 1 || p->W > ANN_MAX_W ||
         p->W * idx->degree > ANN_MAX_STEP_CAND ||
-        (p->hash_bits != 0 && (p->hash_bits < 8 || p->hash_bits > 15)))
+        (p->hash_bits != 0 && (p->hash_bits < 8 || p->hash_bits > 15)) || p->stage_rows < 0 ||
+        p->stage_rows > 32)
         return ANN_ERR_INVALID_ARG;
     if (p->flags & ~ANN_SEARCH_RERANK)
         return ANN_ERR_INVALID_ARG;
-    if (p->flags & ANN_SEARCH_RERANK)
-        return ANN_ERR_UNSUPPORTED;
+    if ((p->flags & ANN_SEARCH_RERANK) && !idx->d_base_f32)
+        return ANN_ERR_UNSUPPORTED;  // the exact rerank needs the fp32 copy of the rows
     if (nq == 0)
         return ANN_OK;
     if (!d_queries || !d_ids || !d_dists)

@@ -70,13 +70,29 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
     return ok != 0;
 }
 
+// Like mbar_try_wait, but the thread may be suspended for up to `hint_ns`
+// nanoseconds waiting for the phase instead of returning at once.
+__device__ __forceinline__ bool mbar_try_wait_hint(uint64_t *bar, uint32_t parity, uint32_t hint_ns)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
+
 // Bounded wait for the phase with the given parity to complete.  Returns false
 // when `max_iters` polls went by without completion (the caller reports a
-// timeout instead of spinning forever).
+// timeout instead of spinning forever).  Each poll may sleep up to 1 us, so
+// a waiting warp leaves its issue slots to the others.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int max_iters)
 {
     for (int i = 0; i < max_iters; ++i)
-        if (mbar_try_wait(bar, parity))
+        if (mbar_try_wait_hint(bar, parity, 1000u))
             return true;
     return false;
 }

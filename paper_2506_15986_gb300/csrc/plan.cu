@@ -1,0 +1,163 @@
+// plan.cu -- batching line: one batch of entry selection + search captured in
+// a CUDA graph (relaunched without host-side launch work), and an autotuner
+// for the knobs that change speed but never results.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <new>
+#include <vector>
+
+#include "internal.h"
+
+struct ann_plan {
+    int device = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+using namespace ann;
+
+extern "C" {
+
+ann_status ann_plan_create(ann_index *idx, const void *d_queries, int64_t nq, int32_t entry_mode, int32_t L_hub,
+                           const ann_search_params *p, int32_t *d_entry_buf, int32_t *d_ids, void *d_dists,
+                           int32_t *d_stats, ann_plan **out)
+{
+    if (!idx || !p || !out || nq < 1 || (entry_mode != ANN_ENTRY_MEDOID && !d_entry_buf))
+        return ANN_ERR_INVALID_ARG;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(idx->device);
+    cudaStream_t s = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        cudaSetDevice(prev);
+        return cuda_status(e);
+    }
+    ann_plan *plan = new (std::nothrow) ann_plan();
+    if (!plan) {
+        cudaStreamDestroy(s);
+        cudaSetDevice(prev);
+        return ANN_ERR_OOM;
+    }
+    plan->device = idx->device;
+    ann_status st = cuda_status(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    ann_status st2 = ANN_OK;
+    if (st == ANN_OK) {
+        const int32_t *entry = nullptr;
+        if (entry_mode != ANN_ENTRY_MEDOID) {
+            st2 = ann_select_entry(idx, d_queries, nq, entry_mode, L_hub, d_entry_buf, nullptr, s);
+            entry = d_entry_buf;
+        }
+        if (st2 == ANN_OK)
+            st2 = ann_search_batch(idx, d_queries, nq, entry, p, d_ids, d_dists, d_stats, s);
+        st = cuda_status(cudaStreamEndCapture(s, &plan->graph));
+    }
+    if (st == ANN_OK && st2 == ANN_OK)
+        st = cuda_status(cudaGraphInstantiate(&plan->exec, plan->graph, 0));
+    cudaStreamDestroy(s);
+    cudaSetDevice(prev);
+    if (st2 != ANN_OK)
+        st = st2;
+    if (st != ANN_OK) {
+        if (plan->exec)
+            cudaGraphExecDestroy(plan->exec);
+        if (plan->graph)
+            cudaGraphDestroy(plan->graph);
+        delete plan;
+        return st;
+    }
+    *out = plan;
+    return ANN_OK;
+}
+
+ann_status ann_plan_launch(ann_plan *plan, void *stream)
+{
+    if (!plan)
+        return ANN_ERR_INVALID_ARG;
+    return cuda_status(cudaGraphLaunch(plan->exec, static_cast<cudaStream_t>(stream)));
+}
+
+ann_status ann_plan_free(ann_plan *plan)
+{
+    if (!plan)
+        return ANN_OK;
+    cudaDeviceSynchronize();
+    if (plan->exec)
+        cudaGraphExecDestroy(plan->exec);
+    if (plan->graph)
+        cudaGraphDestroy(plan->graph);
+    delete plan;
+    return ANN_OK;
+}
+
+ann_status ann_autotune(ann_index *idx, const void *d_queries, int64_t nq, const int32_t *d_entry,
+                        const ann_search_params *p, int32_t *d_ids, void *d_dists, int32_t reps,
+                        ann_search_params *best, float *best_ms, void *stream)
+{
+    if (!idx || !p || !best || nq < 1 || reps < 1)
+        return ANN_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(idx->device);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    // visited-table sizes around the default, and gather round sizes
+    int hb0 = 10;
+    while ((1 << hb0) * 3 / 4 < 12 * p->L && hb0 < 13)
+        ++hb0;
+    std::vector<int> hbs;
+    for (int hb = hb0 - 3; hb <= hb0; ++hb)
+        if (hb >= 8 && hb <= 15)
+            hbs.push_back(hb);
+    const int srs[] = {4, 8, 16};
+    float bms = 1e30f;
+    ann_search_params bp = *p;
+    ann_status st = ANN_OK;
+    for (int hb : hbs) {
+        for (int sr : srs) {
+            ann_search_params c = *p;
+            c.hash_bits = hb;
+            c.stage_rows = sr;
+            st = ann_search_batch(idx, d_queries, nq, d_entry, &c, d_ids, d_dists, nullptr, s);  // warm-up
+            if (st == ANN_ERR_UNSUPPORTED) {  // does not fit in shared memory
+                st = ANN_OK;
+                continue;
+            }
+            if (st != ANN_OK)
+                break;
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < reps && st == ANN_OK; ++r)
+                st = ann_search_batch(idx, d_queries, nq, d_entry, &c, d_ids, d_dists, nullptr, s);
+            cudaEventRecord(e1, s);
+            if (st != ANN_OK)
+                break;
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                st = ANN_ERR_CUDA;
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms /= reps;
+            if (ms < bms) {
+                bms = ms;
+                bp = c;
+            }
+        }
+        if (st != ANN_OK)
+            break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaSetDevice(prev);
+    if (st != ANN_OK)
+        return st;
+    *best = bp;
+    if (best_ms)
+        *best_ms = bms;
+    return ANN_OK;
+}
+
+}  // extern "C"

@@ -52,6 +52,7 @@ struct SearchArgs {
     int32_t *out_ids;
     void *out_dists;
     int32_t *out_stats;
+    int32_t *pool_out;  // optional: the whole final pool (nq x L ids, -1 padded)
     int *status;
     unsigned long long *counter;
     uint32_t *spill;
@@ -108,16 +109,20 @@ __device__ __forceinline__ int visit(uint32_t *htab, int hbits, bool global_mode
     return -1;
 }
 
-// distance of one staged row to the query, as order-preserving key bits
+// Distance of one staged row to the query, computed by a group of 8 lanes
+// (sub = lane % 8 takes the row's 16-byte chunks sub, sub+8, ...) and
+// combined with three xor-shuffles inside the group; every lane of the group
+// returns the order-preserving key bits.  The whole warp must call it.
 template <int DT, int MT>
-__device__ __forceinline__ uint32_t row_distance(const uint8_t *row, const uint8_t *q, int dim)
+__device__ __forceinline__ uint32_t group_distance(const uint8_t *row, const uint8_t *q, int rowbytes, int sub)
 {
+    const int chunks = rowbytes / 16;
     if constexpr (DT == ANN_U8) {
         const uint4 *x4 = reinterpret_cast<const uint4 *>(row);
         const uint4 *q4 = reinterpret_cast<const uint4 *>(q);
         uint32_t acc = 0;
-        for (int c = 0; c < dim / 16; ++c) {
-            uint4 x = x4[c], y = q4[c];
+        for (int c = sub; c < chunks; c += 8) {
+            const uint4 x = x4[c], y = q4[c];
             uint32_t d;
             d = __vabsdiffu4(x.x, y.x);
             acc = __dp4a(d, d, acc);
@@ -128,34 +133,37 @@ __device__ __forceinline__ uint32_t row_distance(const uint8_t *row, const uint8
             d = __vabsdiffu4(x.w, y.w);
             acc = __dp4a(d, d, acc);
         }
+        acc += __shfl_xor_sync(kFull, acc, 4);
+        acc += __shfl_xor_sync(kFull, acc, 2);
+        acc += __shfl_xor_sync(kFull, acc, 1);
         return acc;  // exact non-negative int32, ordered as unsigned
     } else {
         const float4 *q4 = reinterpret_cast<const float4 *>(q);
-        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        float a0 = 0.f, a1 = 0.f;
         auto acc4 = [&](float x0, float x1, float x2, float x3, float4 y) {
             if constexpr (MT == ANN_L2) {
-                float d0 = x0 - y.x, d1 = x1 - y.y, d2 = x2 - y.z, d3 = x3 - y.w;
+                const float d0 = x0 - y.x, d1 = x1 - y.y, d2 = x2 - y.z, d3 = x3 - y.w;
                 a0 = fmaf(d0, d0, a0);
                 a1 = fmaf(d1, d1, a1);
-                a2 = fmaf(d2, d2, a2);
-                a3 = fmaf(d3, d3, a3);
+                a0 = fmaf(d2, d2, a0);
+                a1 = fmaf(d3, d3, a1);
             } else {
                 a0 = fmaf(x0, y.x, a0);
                 a1 = fmaf(x1, y.y, a1);
-                a2 = fmaf(x2, y.z, a2);
-                a3 = fmaf(x3, y.w, a3);
+                a0 = fmaf(x2, y.z, a0);
+                a1 = fmaf(x3, y.w, a1);
             }
         };
         if constexpr (DT == ANN_F32) {
             const float4 *x4 = reinterpret_cast<const float4 *>(row);
-            for (int c = 0; c < dim / 4; ++c) {
-                float4 x = x4[c];
+            for (int c = sub; c < chunks; c += 8) {
+                const float4 x = x4[c];
                 acc4(x.x, x.y, x.z, x.w, q4[c]);
             }
         } else {
             const uint4 *x8 = reinterpret_cast<const uint4 *>(row);
-            for (int c = 0; c < dim / 8; ++c) {
-                uint4 x = x8[c];
+            for (int c = sub; c < chunks; c += 8) {
+                const uint4 x = x8[c];
                 float2 f0, f1, f2, f3;
                 if constexpr (DT == ANN_F16) {
                     f0 = __half22float2(*reinterpret_cast<const __half2 *>(&x.x));
@@ -172,7 +180,10 @@ __device__ __forceinline__ uint32_t row_distance(const uint8_t *row, const uint8
                 acc4(f2.x, f2.y, f3.x, f3.y, q4[2 * c + 1]);
             }
         }
-        float s = (a0 + a1) + (a2 + a3);
+        float s = a0 + a1;
+        s += __shfl_xor_sync(kFull, s, 4);
+        s += __shfl_xor_sync(kFull, s, 2);
+        s += __shfl_xor_sync(kFull, s, 1);
         if constexpr (MT == ANN_IP)
             s = -s;
         return f32_to_ord(s);
@@ -230,6 +241,9 @@ __global__ void __launch_bounds__(32 * kSearchWarps) beam_search_kernel(const Se
         }
 
         int cnt = 0, cursor = 0, evals = 0, hops = 0, hused = 0, gused = 0;
+        int spec_n = 0;  // entries speculated by the previous step (adjacency in spec0/spec1)
+        int32_t spec0 = -1, spec1 = -1;
+        int32_t *spec_old = sel + ANN_MAX_W, *spec_new = sel + 2 * ANN_MAX_W;
         bool gmode = false, found = false;
         if (!failed) {
             // query row -> shared memory; clear the visited table
@@ -271,9 +285,14 @@ __global__ void __launch_bounds__(32 * kSearchWarps) beam_search_kernel(const Se
                         break;
                     }
                     phase ^= 1u;
-                    for (int j = lane; j < ch; j += 32)
-                        cbuf[c0 + j] = make_key(
-                            row_distance<DT, MT>(stage + j * a.stage_stride, qbuf, a.dim), cids[c0 + j]);
+                    // 8 lanes per staged row, 4 rows per pass
+                    for (int r0 = 0; r0 < ch; r0 += 4) {
+                        const int r = r0 + (lane >> 3);
+                        const uint32_t bits = group_distance<DT, MT>(stage + min(r, ch - 1) * a.stage_stride,
+                                                                     qbuf, a.rowbytes, lane & 7);
+                        if (r < ch && (lane & 7) == 0)
+                            cbuf[c0 + r] = make_key(bits, cids[c0 + r]);
+                    }
                     __syncwarp();
                     fence_proxy_async_smem();  // stage reads done before the next bulk writes
                 }
@@ -322,32 +341,62 @@ __global__ void __launch_bounds__(32 * kSearchWarps) beam_search_kernel(const Se
             if (found)
                 break;
 
-            // ---- select the first W unexpanded pool entries
-            int ns = 0, first = -1;
-            for (int i0 = cursor; i0 < cnt && ns < a.W; i0 += 32) {
+            // ---- select the first W unexpanded pool entries (marked expanded)
+            // and the W after them (not marked: they are usually the next
+            // step's choice, so their adjacency rows are fetched one step ahead)
+            int nf = 0, first = -1;
+            for (int i0 = cursor; i0 < cnt && nf < 2 * a.W; i0 += 32) {
                 const int i = i0 + lane;
                 const bool un = i < cnt && !(pool[i] & 1ull);
                 const unsigned um = __ballot_sync(kFull, un);
                 if (um) {
                     if (first < 0)
                         first = i0 + __ffs(um) - 1;
-                    const int rank = __popc(um & lanemask_lt());
-                    if (un && ns + rank < a.W) {
+                    const int g = nf + __popc(um & lanemask_lt());
+                    if (un && g < a.W) {
                         const uint64_t v = pool[i];
                         pool[i] = v | 1ull;
-                        sel[ns + rank] = key_id(v);
+                        sel[g] = key_id(v);
+                    } else if (un && g < 2 * a.W) {
+                        spec_new[g - a.W] = key_id(pool[i]);
                     }
-                    ns = min(a.W, ns + __popc(um));
+                    nf = min(2 * a.W, nf + __popc(um));
                 }
             }
             __syncwarp();
+            const int ns = min(nf, a.W);
             if (ns == 0)
                 break;
             cursor = first;
             hops += ns;
 
-            // ---- neighbours of the selected entries: visited test, compaction
+            // ---- adjacency rows of the selected entries: taken from last step's
+            // speculative fetch when it named the same entries, else loaded now
             const int total = ns * a.R;
+            bool hit = ns == spec_n;
+            for (int s = 0; s < ns && hit; ++s)
+                hit = sel[s] == spec_old[s];
+            int32_t cur0 = spec0, cur1 = spec1;
+            if (!hit) {
+                cur0 = lane < total ? __ldg(a.graph + static_cast<int64_t>(sel[lane / a.R]) * a.R + lane % a.R) : -1;
+                cur1 = lane + 32 < total
+                           ? __ldg(a.graph + static_cast<int64_t>(sel[(lane + 32) / a.R]) * a.R + (lane + 32) % a.R)
+                           : -1;
+            }
+            spec_n = nf - ns;
+            {
+                const int tsp = spec_n * a.R;
+                spec0 = lane < tsp ? __ldg(a.graph + static_cast<int64_t>(spec_new[lane / a.R]) * a.R + lane % a.R)
+                                   : -1;
+                spec1 = lane + 32 < tsp ? __ldg(a.graph + static_cast<int64_t>(spec_new[(lane + 32) / a.R]) * a.R +
+                                                (lane + 32) % a.R)
+                                        : -1;
+                int32_t *t = spec_old;
+                spec_old = spec_new;
+                spec_new = t;
+            }
+
+            // ---- neighbours of the selected entries: visited test, compaction
             if (!gmode && hused + total > hlimit) {
                 gmode = true;  // freeze the shared table, continue in global scratch
                 for (int o = lane; o < (1 << a.spill_bits) / 4; o += 32)
@@ -364,11 +413,7 @@ __global__ void __launch_bounds__(32 * kSearchWarps) beam_search_kernel(const Se
             bool bad = false;
             for (int t0 = 0; t0 < total; t0 += 32) {
                 const int t = t0 + lane;
-                int32_t id = -1;
-                if (t < total) {
-                    const int s = t / a.R;
-                    id = __ldg(a.graph + static_cast<int64_t>(sel[s]) * a.R + (t - s * a.R));
-                }
+                const int32_t id = t < total ? (t0 == 0 ? cur0 : cur1) : -1;
                 int r = 0;
                 if (id >= 0 && id < a.n)
                     r = visit(htab, a.hash_bits, gmode, gtab, a.spill_bits, id);
@@ -416,6 +461,10 @@ __global__ void __launch_bounds__(32 * kSearchWarps) beam_search_kernel(const Se
                 reinterpret_cast<float *>(a.out_dists)[qi * a.k + j] =
                     id >= 0 ? ord_to_f32(db) : __int_as_float(0x7f800000);
         }
+        if (a.pool_out) {
+            for (int j = lane; j < a.L; j += 32)
+                a.pool_out[qi * a.L + j] = (!failed && j < cnt) ? key_id(pool[j]) : -1;
+        }
         if (a.out_stats && lane == 0) {
             const bool miss = failed || (target >= 0 && !found);
             a.out_stats[2 * qi] = miss && target >= 0 ? INT32_MAX : evals;
@@ -424,6 +473,74 @@ __global__ void __launch_bounds__(32 * kSearchWarps) beam_search_kernel(const Se
         __syncwarp();
         if (timed_out)
             return;  // this team's barrier state is unknown: retire it
+    }
+}
+
+// Exact rerank of the final pool (reduced-precision storage): one warp per
+// query re-scores every pool id against the fp32 copy of its row (lanes over
+// the row, FP32 accumulation), sorts the (distance, id) keys in shared memory
+// with a bitonic network and writes the best k.
+constexpr int kRerankWarps = 4;
+
+template <int MT>
+__global__ void __launch_bounds__(32 * kRerankWarps)
+    rerank_kernel(const float *base_f32, int dim, const float *queries, int64_t nq, int64_t qdiv,
+                  const int32_t *pool, int L, int P, int k, const int32_t *dk, int32_t *out_ids,
+                  float *out_dists)
+{
+    extern __shared__ __align__(16) uint64_t rkeys[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint64_t *keys = rkeys + static_cast<size_t>(w) * P;
+    for (int64_t qi = static_cast<int64_t>(blockIdx.x) * kRerankWarps + w; qi < nq;
+         qi += static_cast<int64_t>(gridDim.x) * kRerankWarps) {
+        const float *q = queries + (qi / qdiv) * dim;
+        for (int c = 0; c < P; ++c) {
+            const int32_t id = c < L ? pool[qi * L + c] : -1;
+            uint64_t key = kKeyMax;
+            if (id >= 0) {
+                const float *x = base_f32 + static_cast<int64_t>(id) * dim;
+                float s = 0.f;
+                for (int j = lane; j < dim; j += 32) {
+                    if constexpr (MT == ANN_L2) {
+                        const float t = x[j] - q[j];
+                        s = fmaf(t, t, s);
+                    } else {
+                        s = fmaf(x[j], q[j], s);
+                    }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1)
+                    s += __shfl_xor_sync(kFull, s, o);
+                key = make_key(f32_to_ord(MT == ANN_IP ? -s : s), id);
+            }
+            if (lane == 0)
+                keys[c] = key;
+        }
+        __syncwarp();
+        for (int kk = 2; kk <= P; kk <<= 1) {
+            for (int j = kk >> 1; j > 0; j >>= 1) {
+                for (int i = lane; i < P; i += 32) {
+                    const int p = i ^ j;
+                    if (p > i) {
+                        const uint64_t a = keys[i], b = keys[p];
+                        const bool asc = (i & kk) == 0;
+                        if ((a > b) == asc) {
+                            keys[i] = b;
+                            keys[p] = a;
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        const int kq = dk ? dk[qi] : k;
+        for (int j = lane; j < k; j += 32) {
+            const uint64_t v = j < kq ? keys[j] : kKeyMax;
+            const bool ok = v != kKeyMax;
+            out_ids[qi * k + j] = ok ? key_id(v) : -1;
+            out_dists[qi * k + j] = ok ? ord_to_f32(static_cast<uint32_t>(v >> 32)) : __int_as_float(0x7f800000);
+        }
+        __syncwarp();
     }
 }
 
@@ -504,14 +621,20 @@ ann_status launch_search(ann_index *idx, const SearchLaunch &L, cudaStream_t s)
     int hb = p->hash_bits;
     if (hb == 0) {
         // searches evaluate about 10-16 nodes per pool slot; size the shared
-        // table for 16 per slot below its 3/4 load limit (the exact global
-        // spill table takes any excess)
+        // table for 12 per slot below its 3/4 load limit (the exact global
+        // spill table takes any excess; ann_autotune refines the choice)
         hb = 10;
-        while ((1 << hb) * 3 / 4 < 16 * p->L && hb < 13)
+        while ((1 << hb) * 3 / 4 < 12 * p->L && hb < 13)
             ++hb;
     }
     a.hash_bits = hb;
-    a.spill_bits = 15;
+    // spill tables hold 40 evaluations per pool slot below 3/4 load (about 3x
+    // the typical count): small enough to stay mostly L2-resident and cheap
+    // to clear when a query starts spilling
+    int sb = 12;
+    while ((1 << sb) * 3 / 4 < 40 * p->L && sb < 15)
+        ++sb;
+    a.spill_bits = sb;
 
     const int maxc = p->W * idx->degree;
     int s16 = idx->rowbytes / 16;
@@ -522,11 +645,11 @@ ann_status launch_search(ann_index *idx, const SearchLaunch &L, cudaStream_t s)
     // average), so 16 rows per gather round keep shared memory per team small
     // (more teams per SM); at most 48 KB staged at once, which also keeps one
     // mbarrier phase's byte count far below its 2^20 limit.
-    a.stage_rows = std::max(1, std::min({maxc, 16, 49152 / a.stage_stride}));
+    a.stage_rows = std::max(1, std::min({maxc, p->stage_rows > 0 ? p->stage_rows : 16, 49152 / a.stage_stride}));
 
     size_t off = 16;  // mbarrier
     a.off_sel = static_cast<int>(off);
-    off = align_up(off + 4 * ANN_MAX_W, 16);
+    off = align_up(off + 4 * 3 * ANN_MAX_W, 16);  // selected + two speculated sets
     a.off_q = static_cast<int>(off);
     off = align_up(off + L.qbytes, 16);
     a.off_stage = static_cast<int>(off);
@@ -569,12 +692,44 @@ ann_status launch_search(ann_index *idx, const SearchLaunch &L, cudaStream_t s)
     }
     a.counter = static_cast<unsigned long long *>(scratch);
     a.spill = reinterpret_cast<uint32_t *>(static_cast<uint8_t *>(scratch) + 256);
+    // exact rerank: the search hands its whole pool to rerank_kernel
+    const bool rerank = (p->flags & ANN_SEARCH_RERANK) != 0;
+    void *pool_buf = nullptr;
+    if (rerank) {
+        st = scratch_alloc(idx, static_cast<size_t>(L.nq) * p->L * 4, s, &pool_buf);
+        if (st != ANN_OK) {
+            if (own)
+                scratch_free(idx, scratch, s);
+            return st;
+        }
+        a.pool_out = static_cast<int32_t *>(pool_buf);
+    }
     cudaError_t e = cudaMemsetAsync(scratch, 0, 8, s);
     if (e == cudaSuccess) {
         ANN_DISPATCH(launch_typed, a, smem, teams, s);
     } else {
         st = cuda_status(e);
     }
+    if (st == ANN_OK && rerank) {
+        int P = 32;
+        while (P < p->L)
+            P <<= 1;
+        const size_t rs = static_cast<size_t>(P) * 8 * kRerankWarps;
+        const unsigned grid = static_cast<unsigned>(std::min<int64_t>((L.nq + kRerankWarps - 1) / kRerankWarps,
+                                                                      static_cast<int64_t>(idx->num_sms) * 16));
+        auto rk = idx->metric == ANN_IP ? rerank_kernel<ANN_IP> : rerank_kernel<ANN_L2>;
+        e = cudaFuncSetAttribute(rk, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(rs));
+        if (e == cudaSuccess) {
+            rk<<<grid, 32 * kRerankWarps, rs, s>>>(idx->d_base_f32, idx->dim,
+                                                    static_cast<const float *>(L.queries), L.nq, a.qdiv,
+                                                    a.pool_out, p->L, P, p->k, p->d_k, L.ids,
+                                                    static_cast<float *>(L.dists));
+            e = cudaGetLastError();
+        }
+        st = cuda_status(e);
+    }
+    if (pool_buf)
+        scratch_free(idx, pool_buf, s);
     if (own)
         scratch_free(idx, scratch, s);
     return st;

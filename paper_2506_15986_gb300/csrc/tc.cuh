@@ -177,7 +177,7 @@ __device__ __forceinline__ int canon_off(int r, int k, int KG)
     return (r >> 3) * (KG * 128) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
 }
 
-constexpr int kTcWaitIters = 1 << 24;
+constexpr int kTcWaitIters = 1 << 22;  // polls of up to 1 us each
 
 // Bounded wait of the whole CTA for the MMAs committed to `bar` (phase
 // `phase`).  On success the phase flips and true is returned uniformly.  If

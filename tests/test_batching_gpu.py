@@ -1,0 +1,106 @@
+"""Batching line on the GPU: one persistent launch over queries with mixed k
+and L (k in {1, 10, 100}, L uniform in [max(32, k), 512], as in the 10M batch
+workload), a CUDA-graph plan of entry selection + search, and the autotuner,
+whose knobs must leave results unchanged."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2506_15986_gb300 import ann, synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+DEV = torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module")
+def case():
+    w = synth.shift_f32(n=15000, nq=600, n_train=0)
+    g, _ = oracle.build_graph(w["base"], K=48, R=32)
+    med = oracle.medoid(w["base"])
+    h = ann.ann_index_create(w["base"], g, med, ann.F32, ann.L2)
+    rng = np.random.default_rng(4)
+    k = rng.choice(np.array([1, 10, 100], np.int32), size=600)
+    lo = np.maximum(32, k)
+    L = (lo + np.floor(rng.random(600) * (513 - lo))).astype(np.int32)
+    yield dict(w, graph=g, medoid=med, h=h, k=k.astype(np.int32), L=L)
+    ann.ann_free_index(h)
+
+
+def _t(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def test_mixed_k_and_L_in_one_launch(case):
+    q = case["queries"]
+    nq = len(q)
+    ids = torch.empty((nq, 100), dtype=torch.int32, device=DEV)
+    dd = torch.empty((nq, 100), dtype=torch.float32, device=DEV)
+    st = torch.empty((nq, 2), dtype=torch.int32, device=DEV)
+    dk, dL, dq = _t(case["k"]), _t(case["L"]), _t(q)  # kept alive until the launch completes
+    p = ann.search_params(100, 512, d_k=dk, d_L=dL)
+    ann.ann_search_batch(case["h"], dq, nq, None, p, ids, dd, st)
+    assert ann.ann_sync_status(case["h"]) == ann.OK
+    oi, od, oe, oh = oracle.search(case["base"], case["graph"], q.astype(np.float64), case["medoid"],
+                                   0, 0, Ls=case["L"], ks=case["k"])
+    gi = ids.cpu().numpy()
+    valid = np.arange(100)[None, :] < case["k"][:, None]
+    assert ((gi == oi) | ~valid).all(1).mean() >= 0.99
+    assert (gi[valid] == oi[valid]).mean() >= 0.999
+    assert (gi[~valid] == -1).all()
+    s = st.cpu().numpy()
+    assert (s[:, 0] == oe).mean() >= 0.99 and (s[:, 1] == oh).mean() >= 0.99
+
+
+def _model(case):
+    H = 128
+    W1, b1, W2, b2, E = synth.model_init(128, H, seed=3)
+    hub_nodes = np.random.default_rng(8).choice(len(case["base"]), H, replace=False).astype(np.int32)
+    ann.ann_set_entry_model(case["h"], 128, W1, b1, W2, b2, hub_nodes, E, 8)
+
+
+@pytest.mark.parametrize("mode", [ann.ENTRY_MEDOID, ann.ENTRY_LEARNED_NAV])
+def test_graph_plan_replays_the_batch(case, mode):
+    if mode != ann.ENTRY_MEDOID:
+        _model(case)
+    q = _t(case["queries"])
+    nq = q.shape[0]
+    p = ann.search_params(10, 64)
+    ref_e = torch.empty(nq, dtype=torch.int32, device=DEV)
+    ref_i = torch.empty((nq, 10), dtype=torch.int32, device=DEV)
+    ref_d = torch.empty((nq, 10), dtype=torch.float32, device=DEV)
+    ent = None
+    if mode != ann.ENTRY_MEDOID:
+        ann.ann_select_entry(case["h"], q, nq, mode, 24, ref_e)
+        ent = ref_e
+    ann.ann_search_batch(case["h"], q, nq, ent, p, ref_i, ref_d)
+    buf = torch.empty(nq, dtype=torch.int32, device=DEV)
+    ids = torch.full((nq, 10), -9, dtype=torch.int32, device=DEV)
+    dd = torch.zeros((nq, 10), dtype=torch.float32, device=DEV)
+    plan = ann.ann_plan_create(case["h"], q, nq, mode, 24, p, buf, ids, dd)
+    try:
+        for _ in range(2):
+            ids.fill_(-9)
+            ann.ann_plan_launch(plan)
+            torch.cuda.synchronize()
+            assert torch.equal(ids, ref_i) and torch.equal(dd, ref_d)
+    finally:
+        ann.ann_plan_free(plan)
+    assert ann.ann_sync_status(case["h"]) == ann.OK
+
+
+def test_autotune_keeps_results(case):
+    q = _t(case["queries"])
+    nq = q.shape[0]
+    p = ann.search_params(10, 128)
+    ids = torch.empty((nq, 10), dtype=torch.int32, device=DEV)
+    dd = torch.empty((nq, 10), dtype=torch.float32, device=DEV)
+    ann.ann_search_batch(case["h"], q, nq, None, p, ids, dd)
+    ref = ids.clone(), dd.clone()
+    best, ms = ann.ann_autotune(case["h"], q, nq, None, p, ids, dd, reps=2)
+    assert ms > 0 and best.hash_bits >= 8 and best.stage_rows in (4, 8, 16)
+    ann.ann_search_batch(case["h"], q, nq, None, best, ids, dd)
+    torch.cuda.synchronize()
+    assert torch.equal(ids, ref[0]) and torch.equal(dd, ref[1])
