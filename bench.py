@@ -1,21 +1,31 @@
 #!/usr/bin/env python3
 """Benchmark: QPS at recall@10 = 0.95 on one GB300, learned vs medoid entry,
-with distance evaluations per query (shifted-query 1M x 128 fp32 workload).
+with distance evaluations per query.
 
+Default workload (`--workload shift`): the shifted-query 1M x 128 fp32 config.
 Setup (untimed, all on the GPU through libann): the synthetic workload, the
 proximity graph (exact 64-NN + RNG pruning, R = 32), exact ground truth, 1,024
 k-means hubs, label-mode search costs for 100,000 training queries, the label
 rule (t_pos = 3, t_neg = 15) and the contrastive training of the two-tower
 entry model (Adam, batch 8,192).
 
-One step = one batch of the 10,000 evaluation queries through the public
-path: ann_select_entry (query tower, then the hub-graph search or the
-exhaustive tensor-core hub scoring, whichever is faster) then ann_search_batch
-(W = 2 pool entries expanded per step, visited-table and gather sizes picked by
-ann_autotune), at the pool size L* that first reaches recall@10 >= 0.95 in the
-L sweep.  `value` is the learned-entry QPS; the medoid-entry numbers (same W,
-own L* and tuning) sit beside it in `config`.  Inputs are resident in HBM when the timed region
-starts; the base set (512 MB) is larger than L2, so no flush is needed.
+One step = one batch of the evaluation queries through the public path:
+ann_select_entry (query tower, then the hub-graph search or the exhaustive
+tensor-core hub scoring, whichever is faster) then ann_search_batch (W = 2
+pool entries expanded per step when the degree allows, visited-table and
+gather sizes picked by ann_autotune), at the pool size L* that first reaches
+recall@10 >= 0.95 in the L sweep.  `value` is the learned-entry QPS; the
+medoid-entry numbers (same W, own L* and tuning) sit beside it in `config`.
+Inputs are resident in HBM when the timed region starts; every base set is
+larger than L2 (129 MB) except the small uint8 one, so no flush is needed.
+
+Other workloads (`--workload`):
+  ip       1M x 200 unit vectors, maximum inner product, out-of-distribution
+           queries, 4,096 hubs; learned vs medoid at recall 0.90 / 0.95 / 0.99
+  highdim  1M x 960 fp32, R = 48, 1,000 shifted queries, medoid entry; fp32
+           storage vs fp16 storage with the exact fp32 rerank, k = 10 and 100,
+           distance error against float64 recomputation
+  small    10,000 x 128 uint8 (the parity config), medoid entry, L = 64
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -41,14 +51,36 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "QPS at recall@10=0.95 on 1 GB300, learned vs medoid entry; dist evals/query"
-WORKLOAD = ("shift_f32: N=1,000,000 fp32 d=128 base (1,000-component anisotropic Gaussian "
-            "mixture, variance spectrum (1+i)^-1), 10,000 shifted/reweighted queries, graph "
-            "exact 64-NN + RNG prune (alpha=1) R=32 with reachability repair, k=10, 1,024 "
-            "k-means hubs, BF16 query tower 128-256-64 trained on 100,000 labelled queries")
 L_SWEEP = [16, 24, 32, 48, 64, 96, 128, 160, 192, 256, 320, 384, 512]
-TARGET = 0.95
 K_NN = 10
-DIM, DEGREE = 128, 32
+
+WORKLOADS = {
+    "shift": dict(
+        desc=("shift_f32: N=1,000,000 fp32 d=128 base (1,000-component anisotropic Gaussian mixture, "
+              "variance spectrum (1+i)^-1), 10,000 shifted/reweighted queries, graph exact 64-NN + RNG "
+              "prune (alpha=1) R=32 with reachability repair, k=10, 1,024 k-means hubs, BF16 query tower "
+              "128-256-64 trained on 100,000 labelled queries"),
+        gen="shift_f32", n=1_000_000, nq=10_000, n_train=100_000, dim=128, R=32, metric="l2",
+        dtype="f32", hubs=1024, learned=True, targets=[0.95]),
+    "ip": dict(
+        desc=("ip_f32: N=1,000,000 unit fp32 d=200 (2,000-component normalised mixture), 10,000 "
+              "queries from a rotated, noisier mixture, maximum inner product, graph exact 64-NN + RNG "
+              "prune R=32, k=10, 4,096 k-means hubs, BF16 query tower 200-256-64 trained on 100,000 "
+              "labelled queries"),
+        gen="ip_f32", n=1_000_000, nq=10_000, n_train=100_000, dim=200, R=32, metric="ip",
+        dtype="f32", hubs=4096, learned=True, targets=[0.90, 0.95, 0.99]),
+    "highdim": dict(
+        desc=("highdim_f32: N=1,000,000 fp32 d=960 (500-component low-rank mixture, 3.84 GB), 1,000 "
+              "mean-shifted queries, graph exact 64-NN + RNG prune R=48, medoid entry, fp32 storage vs "
+              "fp16 storage with exact fp32 rerank"),
+        gen="highdim_f32", n=1_000_000, nq=1_000, n_train=0, dim=960, R=48, metric="l2",
+        dtype="f32", hubs=0, learned=False, targets=[0.95], precision=True),
+    "small": dict(
+        desc=("small_u8: N=10,000 uint8 d=128 (50-component mixture), 100 queries, graph exact 64-NN + "
+              "RNG prune R=32, medoid entry, L=64, k=10"),
+        gen="small_u8", n=10_000, nq=100, n_train=0, dim=128, R=32, metric="l2", dtype="u8",
+        hubs=0, learned=False, targets=[0.0], fixed_L=64),
+}
 
 
 def parse():
@@ -57,10 +89,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--n", type=int, default=1_000_000, help="base size")
-    ap.add_argument("--nq", type=int, default=10_000)
-    ap.add_argument("--n-train", type=int, default=100_000)
-    ap.add_argument("--hubs", type=int, default=1024)
+    ap.add_argument("--workload", default="shift", choices=sorted(WORKLOADS))
+    ap.add_argument("--n", type=int, default=0, help="base size (0: the workload's)")
+    ap.add_argument("--nq", type=int, default=0, help="evaluation queries (0: the workload's)")
+    ap.add_argument("--n-train", type=int, default=-1)
+    ap.add_argument("--hubs", type=int, default=0)
     ap.add_argument("--epochs", type=int, default=200)
     ap.add_argument("--lr", type=float, default=5e-5)
     ap.add_argument("--tau", type=float, default=0.07)
@@ -72,7 +105,26 @@ def parse():
     ap.add_argument("--no-tune", action="store_true", help="skip ann_autotune at L*")
     ap.add_argument("--fixed-L", type=int, default=0,
                     help="skip the L sweep and run every entry mode at this pool size")
-    return ap.parse_args()
+    args = ap.parse_args()
+    spec = dict(WORKLOADS[args.workload])
+    if args.n:
+        spec["n"] = args.n
+    if args.nq:
+        spec["nq"] = args.nq
+    if args.n_train >= 0:
+        spec["n_train"] = args.n_train
+    if args.hubs:
+        spec["hubs"] = args.hubs
+    if args.no_learned:
+        spec["learned"] = False
+    if not spec["learned"]:
+        spec["n_train"] = 0
+    if args.fixed_L:
+        spec["fixed_L"] = args.fixed_L
+    # W * R may not exceed 64 candidates per step
+    args.W = max(1, min(args.W, 64 // spec["R"]))
+    args.spec = spec
+    return args
 
 
 def dist_env():
@@ -143,42 +195,63 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def recall(ids, gt):
+def recall(ids, gt, k=K_NN):
     hits = 0
-    for a, b in zip(ids, gt):
+    for a, b in zip(ids[:, :k], gt[:, :k]):
         hits += len(np.intersect1d(a[a >= 0], b))
-    return hits / gt.size
+    return hits / (len(gt) * k)
 
 
-def build_workload(args, torch, ann, synth, dev, n_train):
+def generate(spec, synth):
+    g = spec["gen"]
+    if g == "shift_f32":
+        return synth.shift_f32(n=spec["n"], nq=spec["nq"], n_train=spec["n_train"])
+    if g == "ip_f32":
+        return synth.ip_f32(n=spec["n"], nq=spec["nq"], n_train=spec["n_train"])
+    if g == "highdim_f32":
+        return synth.highdim_f32(n=spec["n"], nq=spec["nq"])
+    return synth.small_u8(n=spec["n"], nq=spec["nq"])
+
+
+def build_workload(args, torch, ann, synth, dev):
+    spec = args.spec
     t0 = time.time()
-    w = synth.shift_f32(n=args.n, nq=args.nq, n_train=n_train)
+    w = generate(spec, synth)
     t_gen = time.time() - t0
+    n, dim, R = spec["n"], spec["dim"], spec["R"]
+    dt = ann.U8 if spec["dtype"] == "u8" else ann.F32
+    metric = ann.IP if spec["metric"] == "ip" else ann.L2
     base = torch.from_numpy(w["base"]).to(dev)
-    graph = torch.empty((args.n, DEGREE), dtype=torch.int32, device=dev)
+    graph = torch.empty((n, R), dtype=torch.int32, device=dev)
     t0 = time.time()
-    med, rep = ann.ann_build_graph(base, args.n, DIM, ann.F32, 64, DEGREE, 1.0, graph)
+    # the graph is built under squared L2; for unit vectors it orders
+    # neighbours exactly as the inner product does
+    med, rep = ann.ann_build_graph(base, n, dim, dt, 64, R, 1.0, graph)
     t_build = time.time() - t0
     q = torch.from_numpy(w["queries"]).to(dev)
-    gt = torch.empty((args.nq, K_NN), dtype=torch.int32, device=dev)
-    gtd = torch.empty((args.nq, K_NN), dtype=torch.float32, device=dev)
-    ann.ann_knn(base, args.n, DIM, ann.F32, ann.L2, q, args.nq, K_NN, gt, gtd)
-    h = ann.ann_index_create(base, graph, med, ann.F32, ann.L2, device=dev.index or 0)
+    nq = q.shape[0]
+    kmax = 100 if spec.get("precision") else K_NN
+    gt = torch.empty((nq, kmax), dtype=torch.int32, device=dev)
+    gtd = torch.empty((nq, kmax), dtype=torch.int32 if dt == ann.U8 else torch.float32, device=dev)
+    ann.ann_knn(base, n, dim, dt, metric, q, nq, kmax, gt, gtd)
+    h = ann.ann_index_create(base, graph, med, dt, metric, device=dev.index or 0)
     return dict(w=w, base=base, graph=graph, medoid=med, repairs=rep, q=q, gt=gt.cpu().numpy(),
-                h=h, t_build=t_build, t_gen=t_gen)
+                h=h, t_build=t_build, t_gen=t_gen, dim=dim, R=R, dt=dt, metric=metric,
+                bytes_per_elem=1 if dt == ann.U8 else 4)
 
 
 def build_learned(W, args, torch, ann, synth, dev):
     """Hubs, labels and training of the entry model, all through libann."""
-    n, H0, M = args.n, args.hubs, args.cand
+    spec = args.spec
+    n, H0, M, dim = spec["n"], spec["hubs"], args.cand, W["dim"]
     times = {}
     t0 = time.time()
     sample = synth.sample_rows(n, min(n, 262_144), seed=synth.SEED_BASE + 10)
     init = synth.kmeans_init(len(sample), H0, seed=synth.SEED_BASE + 11)
-    cent = torch.empty((H0, DIM), dtype=torch.float32, device=dev)
-    obj = ann.ann_kmeans(W["base"], n, DIM, ann.F32, sample, H0, init, 25, cent)
+    cent = torch.empty((H0, dim), dtype=torch.float32, device=dev)
+    obj = ann.ann_kmeans(W["base"], n, dim, ann.F32, sample, H0, init, 25, cent)
     hubs = torch.empty(H0, dtype=torch.int32, device=dev)
-    ann.ann_assign_hubs(W["base"], n, DIM, ann.F32, cent, H0, hubs)
+    ann.ann_assign_hubs(W["base"], n, dim, ann.F32, cent, H0, hubs)
     hub_np = hubs.cpu().numpy()
     hub_np = hub_np[hub_np >= 0]
     H = len(hub_np)
@@ -191,10 +264,10 @@ def build_learned(W, args, torch, ann, synth, dev):
     nt = tq.shape[0]
     cand = torch.empty((nt, M), dtype=torch.int32, device=dev)
     cd = torch.empty((nt, M), dtype=torch.float32, device=dev)
-    ann.ann_knn(hub_vecs, H, DIM, ann.F32, ann.L2, tq, nt, M, cand, cd)
+    ann.ann_knn(hub_vecs, H, dim, ann.F32, W["metric"], tq, nt, M, cand, cd)
     tgt = torch.empty((nt, 1), dtype=torch.int32, device=dev)
     td = torch.empty((nt, 1), dtype=torch.float32, device=dev)
-    ann.ann_knn(W["base"], n, DIM, ann.F32, ann.L2, tq, nt, 1, tgt, td)
+    ann.ann_knn(W["base"], n, dim, ann.F32, W["metric"], tq, nt, 1, tgt, td)
     ev = torch.empty((nt, M), dtype=torch.int32, device=dev)
     hp = torch.empty_like(ev)
     ann.ann_hub_costs(W["h"], tq, nt, tgt, cand, M, hub_nodes, 64, ev, hp)
@@ -208,14 +281,14 @@ def build_learned(W, args, torch, ann, synth, dev):
     times["labels_s"] = time.time() - t0
 
     t0 = time.time()
-    W1, b1, W2, b2, E = synth.model_init(DIM, H)
+    W1, b1, W2, b2, E = synth.model_init(dim, H)
     # hub tower starts at the query tower applied to each hub's own vector
-    ann.ann_set_entry_model(W["h"], DIM, W1, b1, W2, b2, hub_np, E, 16)
+    ann.ann_set_entry_model(W["h"], dim, W1, b1, W2, b2, hub_np, E, 16)
     E0 = torch.empty((H, 64), dtype=torch.float32, device=dev)
     tmp = torch.empty(H, dtype=torch.int32, device=dev)
     ann.ann_select_entry(W["h"], hub_vecs, H, ann.ENTRY_LEARNED_EXHAUSTIVE, args.l_hub, tmp, E0)
     batch = 8192
-    t = ann.ann_trainer_create(DIM, W1, b1, W2, b2, E0, batch, tau=args.tau, lr=args.lr)
+    t = ann.ann_trainer_create(dim, W1, b1, W2, b2, E0, batch, tau=args.tau, lr=args.lr)
     order = torch.from_numpy(np.concatenate(
         synth.train_batches(nt, batch, args.epochs, seed=synth.SEED_BASE + 12))).to(dev)
     spe = (nt + batch - 1) // batch
@@ -235,26 +308,29 @@ def build_learned(W, args, torch, ann, synth, dev):
 class Runner:
     """One step = entry selection (learned modes) + batched search."""
 
-    def __init__(self, W, torch, ann, args, mode):
+    def __init__(self, W, torch, ann, args, mode, h=None, flags=0, k=K_NN):
         self.W, self.torch, self.ann, self.mode, self.args = W, torch, ann, mode, args
+        self.h = W["h"] if h is None else h
+        self.flags, self.k = flags, k
         dev = W["q"].device
         nq = W["q"].shape[0]
         self.nq = nq
         self.stream = torch.cuda.current_stream()
-        self.ids = torch.empty((nq, K_NN), dtype=torch.int32, device=dev)
-        self.dists = torch.empty((nq, K_NN), dtype=torch.float32, device=dev)
+        self.ids = torch.empty((nq, k), dtype=torch.int32, device=dev)
+        dd = torch.int32 if W["dt"] == ann.U8 else torch.float32
+        self.dists = torch.empty((nq, k), dtype=dd, device=dev)
         self.stats = torch.empty((nq, 2), dtype=torch.int32, device=dev)
         self.entry = torch.empty(nq, dtype=torch.int32, device=dev)
         self.tuned = {}  # L -> ann_search_params picked by ann_autotune
 
     def params(self, L):
-        return self.tuned.get(L) or self.ann.search_params(K_NN, L, W=self.args.W)
+        return self.tuned.get(L) or self.ann.search_params(self.k, L, W=self.args.W, flags=self.flags)
 
     def autotune(self, L):
         """Pick the visited-table size and gather round size (speed-only knobs)."""
         q = self.W["q"]
         e = self.select(q)
-        best, ms = self.ann.ann_autotune(self.W["h"], q, self.nq, e, self.params(L), self.ids,
+        best, ms = self.ann.ann_autotune(self.h, q, self.nq, e, self.params(L), self.ids,
                                          self.dists, 3, self.stream)
         self.tuned[L] = best
         return {"hash_bits": best.hash_bits, "stage_rows": best.stage_rows, "search_ms": ms}
@@ -263,31 +339,36 @@ class Runner:
         if self.mode == "medoid":
             return None
         m = self.ann.ENTRY_LEARNED_NAV if self.mode == "learned" else self.ann.ENTRY_LEARNED_EXHAUSTIVE
-        self.ann.ann_select_entry(self.W["h"], q, self.nq, m, self.args.l_hub, self.entry, None,
+        self.ann.ann_select_entry(self.h, q, self.nq, m, self.args.l_hub, self.entry, None,
                                   self.stream)
         return self.entry
 
     def search(self, q, entry, L, stats=False):
-        self.ann.ann_search_batch(self.W["h"], q, self.nq, entry, self.params(L),
-                                  self.ids, self.dists, self.stats if stats else None, self.stream)
+        self.ann.ann_search_batch(self.h, q, self.nq, entry, self.params(L), self.ids, self.dists,
+                                  self.stats if stats else None, self.stream)
 
     def step(self, L, q=None, stats=False):
         q = self.W["q"] if q is None else q
         self.search(q, self.select(q), L, stats)
 
     def launches(self):
-        return {"medoid": 1, "learned": 4, "exhaustive": 3}[self.mode]
+        extra = 1 if self.flags else 0
+        return {"medoid": 1, "learned": 4, "exhaustive": 3}[self.mode] + extra
 
 
-def sweep(run, torch, ann, W):
-    """recall@10, evals, QPS per L; L* = the smallest swept L with recall@10 >=
-    0.95; QPS at exactly 0.95 interpolated between the bracketing L."""
+def sweep(run, torch, ann, W, targets):
+    """recall@k, evals, QPS per L (until the highest target is reached twice);
+    per target: the smallest swept L reaching it and the QPS interpolated at
+    exactly the target between the bracketing L."""
     out = []
+    top = max(targets)
     for L in L_SWEEP:
+        if L < run.k:
+            continue
         run.step(L, stats=True)
-        if ann.ann_sync_status(W["h"], run.stream) != ann.OK:
+        if ann.ann_sync_status(run.h, run.stream) != ann.OK:
             raise RuntimeError("search reported a device error")
-        r = recall(run.ids.cpu().numpy(), W["gt"])
+        r = recall(run.ids.cpu().numpy(), W["gt"], run.k)
         s = run.stats.cpu().numpy()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(run.stream)
@@ -297,18 +378,22 @@ def sweep(run, torch, ann, W):
         torch.cuda.synchronize()
         out.append(dict(L=L, recall=r, evals=float(s[:, 0].mean()), hops=float(s[:, 1].mean()),
                         qps=run.nq * 5 / (e0.elapsed_time(e1) / 1e3)))
-        if len([x for x in out if x["recall"] >= TARGET]) >= 2:
+        if len([x for x in out if x["recall"] >= top]) >= 2:
             break
-    hit = [x for x in out if x["recall"] >= TARGET]
-    Lstar = hit[0]["L"] if hit else out[-1]["L"]
-    interp = None
-    if out[0]["recall"] >= TARGET:
-        interp = out[0]["qps"]
-    for a, b in zip(out, out[1:]):
-        if a["recall"] < TARGET <= b["recall"]:
-            t = (TARGET - a["recall"]) / (b["recall"] - a["recall"])
-            interp = a["qps"] + t * (b["qps"] - a["qps"])
-    return Lstar, out, interp
+    per = {}
+    for t in targets:
+        hit = [x for x in out if x["recall"] >= t]
+        interp = None
+        if out and out[0]["recall"] >= t:
+            interp = out[0]["qps"]
+        for a, b in zip(out, out[1:]):
+            if a["recall"] < t <= b["recall"]:
+                f = (t - a["recall"]) / (b["recall"] - a["recall"])
+                interp = a["qps"] + f * (b["qps"] - a["qps"])
+        per[t] = dict(L=hit[0]["L"] if hit else None, qps_interp=interp)
+    main = targets[0] if len(targets) == 1 else 0.95
+    Lstar = per[main]["L"] or out[-1]["L"]
+    return Lstar, out, per
 
 
 def timed(run, torch, ann, args, L, world, dev):
@@ -351,8 +436,8 @@ def end_to_end(run, torch, L, steps):
     queries, entry selection + search, D2H of ids and distances, every step."""
     W = run.W
     qh = torch.from_numpy(W["w"]["queries"]).pin_memory()
-    ih = torch.empty((run.nq, K_NN), dtype=torch.int32).pin_memory()
-    dh = torch.empty((run.nq, K_NN), dtype=torch.float32).pin_memory()
+    ih = torch.empty(tuple(run.ids.shape), dtype=run.ids.dtype).pin_memory()
+    dh = torch.empty(tuple(run.dists.shape), dtype=run.dists.dtype).pin_memory()
     qd = torch.empty_like(W["q"])
     for i in range(steps + 3):
         if i == 3:
@@ -365,26 +450,27 @@ def end_to_end(run, torch, L, steps):
         run.stream.synchronize()
     dt = time.perf_counter() - a0
     return {"value": run.nq * steps / dt, "unit": "queries/s",
-            "h2d_bytes_per_step": int(qh.numel() * 4),
+            "h2d_bytes_per_step": int(qh.numel() * qh.element_size()),
             "d2h_bytes_per_step": int(ih.numel() * 4 + dh.numel() * 4)}
 
 
-def cpu_baseline(W, L, entries=None, target_s=10.0, width=1):
+def cpu_baseline(W, L, entries=None, target_s=10.0, width=1, k=K_NN):
     """The oracle's search on the host cores on a bounded sample of the
     evaluation queries sized to take about target_s seconds."""
     import oracle
     base = W["w"]["base"]
     g = W["graph"].cpu().numpy()
     allq = W["w"]["queries"].astype(np.float64)
+    metric = oracle.IP if W["metric"] == 1 else oracle.L2
     oracle.build()
     ent = np.full(len(allq), W["medoid"], np.int32) if entries is None else entries
     probe = min(len(allq), 4 * oracle.num_threads())
     t = time.perf_counter()
-    oracle.search(base, g, allq[:probe], ent[:probe], L, K_NN, W=width)
+    oracle.search(base, g, allq[:probe], ent[:probe], L, k, W=width, metric=metric)
     per_q = (time.perf_counter() - t) / probe
     m = int(min(len(allq), max(probe, target_s / max(per_q, 1e-9))))
     t = time.perf_counter()
-    ids, _, ev, _ = oracle.search(base, g, allq[:m], ent[:m], L, K_NN, W=width)
+    ids, _, ev, _ = oracle.search(base, g, allq[:m], ent[:m], L, k, W=width, metric=metric)
     dt = time.perf_counter() - t
     return {"value": m / dt, "unit": "queries/s", "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"first {m} of the {len(allq)} evaluation queries at L={L}, W={width}, "
@@ -393,10 +479,65 @@ def cpu_baseline(W, L, entries=None, target_s=10.0, width=1):
             "recall@10_sample": recall(ids, W["gt"][:m]), "evals_per_query": float(ev.mean())}
 
 
+def measure_mode(run, torch, ann, W, args, targets):
+    if args.spec.get("fixed_L"):
+        Lstar, sw, per = args.spec["fixed_L"], [], {}
+    else:
+        Lstar, sw, per = sweep(run, torch, ann, W, targets)
+    tune = None if args.no_tune else run.autotune(Lstar)
+    run.step(Lstar, stats=True)
+    torch.cuda.synchronize()
+    s = run.stats.cpu().numpy().astype(np.int64)
+    b = W["bytes_per_elem"] if not run.flags else 2
+    return dict(L=Lstar, sweep=sw, per_target=per, run=run, tune=tune,
+                recall=recall(run.ids.cpu().numpy(), W["gt"], run.k),
+                evals=float(s[:, 0].mean()), hops=float(s[:, 1].mean()),
+                alg_bytes=int((s[:, 0] * W["dim"] * b + s[:, 1] * W["R"] * 4).sum()
+                              + run.nq * W["dim"] * 4),
+                entries=None if run.mode == "medoid" else run.entry.cpu().numpy())
+
+
+def precision_report(W, torch, ann, args, dev):
+    """fp16 storage + exact fp32 rerank against fp32 storage (k = 10 and 100),
+    with the distance error of each against float64 recomputation."""
+    base = W["w"]["base"]
+    h16 = ann.ann_index_create(base.astype(np.float16), W["graph"], W["medoid"], ann.F16, W["metric"],
+                               device=dev.index or 0, base_f32=base)
+    out = {}
+    q = W["w"]["queries"].astype(np.float64)
+    try:
+        for k in (10, 100):
+            for name, h, flags in (("fp32", W["h"], 0), ("fp16_rerank", h16, ann.SEARCH_RERANK),
+                                   ("fp16", h16, 0)):
+                run = Runner(W, torch, ann, args, "medoid", h=h, flags=flags, k=k)
+                Lstar, sw, per = sweep(run, torch, ann, W, [0.95])
+                tm, sm, _ = timed(run, torch, ann, argparse.Namespace(warmup=2, steps=20), Lstar, 1, dev)
+                run.step(Lstar)
+                torch.cuda.synchronize()
+                ids = run.ids.cpu().numpy()
+                d = run.dists.cpu().numpy().astype(np.float64)
+                rel = []
+                for i in range(0, len(q), max(1, len(q) // 100)):
+                    ok = ids[i] >= 0
+                    diff = base[ids[i][ok]].astype(np.float64) - q[i]
+                    d64 = (diff * diff).sum(1)
+                    rel.append(np.abs(d[i][ok] - d64) / np.maximum(d64, 1e-30))
+                rel = np.concatenate(rel)
+                out[f"{name}_k{k}"] = dict(L=Lstar, recall=recall(ids, W["gt"], k),
+                                           qps=run.nq * 20 / (tm / 1e3),
+                                           qps_interp_0_95=per[0.95]["qps_interp"],
+                                           max_rel_dist_err_vs_fp64=float(rel.max()),
+                                           mean_rel_dist_err_vs_fp64=float(rel.mean()))
+    finally:
+        ann.ann_free_index(h16)
+    return out
+
+
 def run_gpu(args):
     import torch
     from paper_2506_15986_gb300 import _build, ann, synth
 
+    spec = args.spec
     rank, world, local = dist_env()
     if world > 1:
         import torch.distributed as distd
@@ -405,25 +546,13 @@ def run_gpu(args):
     dev = torch.device("cuda", local)
     _build.build()
     ann.load_library()
-    W = build_workload(args, torch, ann, synth, dev, 0 if args.no_learned else args.n_train)
-    learned = None if args.no_learned else build_learned(W, args, torch, ann, synth, dev)
+    W = build_workload(args, torch, ann, synth, dev)
+    learned = build_learned(W, args, torch, ann, synth, dev) if spec["learned"] else None
+    targets = spec["targets"]
 
     res = {}
-    for mode in (["medoid"] if args.no_learned else ["medoid", "learned", "exhaustive"]):
-        run = Runner(W, torch, ann, args, mode)
-        if args.fixed_L:
-            Lstar, sw, interp = args.fixed_L, [], None
-        else:
-            Lstar, sw, interp = sweep(run, torch, ann, W)
-        tune = None if args.no_tune else run.autotune(Lstar)
-        run.step(Lstar, stats=True)
-        torch.cuda.synchronize()
-        s = run.stats.cpu().numpy().astype(np.int64)
-        res[mode] = dict(L=Lstar, sweep=sw, qps_interp=interp, run=run,
-                         recall=recall(run.ids.cpu().numpy(), W["gt"]),
-                         evals=float(s[:, 0].mean()), hops=float(s[:, 1].mean()),
-                         alg_bytes=int((s[:, 0] * DIM * 4 + s[:, 1] * DEGREE * 4).sum() + run.nq * DIM * 4),
-                         entries=None if mode == "medoid" else run.entry.cpu().numpy(), tune=tune)
+    for mode in (["medoid", "learned", "exhaustive"] if spec["learned"] else ["medoid"]):
+        res[mode] = measure_mode(Runner(W, torch, ann, args, mode), torch, ann, W, args, targets)
     # a short timing of every mode picks the headline: the faster learned mode
     # (hub-graph search or exhaustive tensor-core hub scoring), medoid without
     # a model; then the headline is timed under the full protocol
@@ -442,23 +571,28 @@ def run_gpu(args):
             tm, sm, _ = timed(r["run"], torch, ann, args, r["L"], 1, dev)
             others[mode] = dict(qps=r["run"].nq * args.steps / (tm / 1e3), L=r["L"],
                                 recall=r["recall"], evals_per_query=r["evals"],
-                                hops_per_query=r["hops"], qps_interpolated_at_0_95=r["qps_interp"],
+                                hops_per_query=r["hops"],
+                                per_target={str(t): v for t, v in r["per_target"].items()},
                                 search_ms=sm, tuned=r["tune"], sweep=r["sweep"])
     e2e = end_to_end(R["run"], torch, R["L"], max(10, args.steps // 4))
     e2e["value"] *= world
+    prec = precision_report(W, torch, ann, args, dev) if spec.get("precision") else None
     peak, peak_kind = peaks()
     achieved = R["alg_bytes"] / (search_ms / 1e3) / 1e9
     out = None
     if rank == 0:
         cpu = None if args.no_cpu else cpu_baseline(W, R["L"], R["entries"], width=args.W)
-        cfg = {"workload": WORKLOAD, "n": args.n, "nq": args.nq, "entry": head, "L": R["L"],
-               "k": K_NN, "recall@10": R["recall"], "evals_per_query": R["evals"],
-               "hops_per_query": R["hops"], "qps_interpolated_at_0.95": R["qps_interp"],
-               "W": args.W, "tuned": R["tune"],
-               "sweep": R["sweep"], "other_entry_modes": others, "l_hub": args.l_hub,
-               "l2": "inputs larger than L2 (512 MB base), no flush",
+        big = spec["n"] * W["dim"] * W["bytes_per_elem"] > 129e6
+        cfg = {"workload": spec["desc"], "n": spec["n"], "nq": R["run"].nq, "entry": head,
+               "L": R["L"], "W": args.W, "k": K_NN, "recall@10": R["recall"],
+               "evals_per_query": R["evals"], "hops_per_query": R["hops"],
+               "per_target": {str(t): v for t, v in R["per_target"].items()},
+               "tuned": R["tune"], "sweep": R["sweep"], "other_entry_modes": others,
+               "l_hub": args.l_hub,
+               "l2": "inputs larger than L2 (129 MB), no flush" if big
+               else "base smaller than L2: an L2-resident parity config",
                "graph_build_s": W["t_build"], "repairs": W["repairs"], "learned": learned,
-               "parallelism": f"replicas{world}"}
+               "precision": prec, "parallelism": f"replicas{world}"}
         if "medoid" in others:
             med = others["medoid"]
             cfg["learned_vs_medoid"] = {
@@ -467,12 +601,11 @@ def run_gpu(args):
         out = {
             "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic", "config": cfg,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u8" if W["dt"] == ann.U8 else "f32", "data": "synthetic", "config": cfg,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None,
-                         "kernel": "beam_search_kernel<F32,L2>",
-                         "peak_kind": f"{peak_kind} copy bandwidth",
+                         "kernel": "beam_search_kernel", "peak_kind": f"{peak_kind} copy bandwidth",
                          "alg_bytes_per_launch": R["alg_bytes"], "launch_ms": search_ms},
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": args.steps * R["run"].launches(),
@@ -494,12 +627,14 @@ def run_reference(args):
     import torch
     from paper_2506_15986_gb300 import _build, ann, synth
 
+    spec = args.spec
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     _build.build()
-    W = build_workload(args, torch, ann, synth, dev, 0)
+    spec["n_train"] = 0
+    W = build_workload(args, torch, ann, synth, dev)
     run = Runner(W, torch, ann, args, "medoid")
-    Lstar = sweep(run, torch, ann, W)[0]
+    Lstar = spec.get("fixed_L") or sweep(run, torch, ann, W, spec["targets"])[0]
     for _ in range(args.warmup):
         cpu_baseline(W, Lstar, target_s=2.0, width=args.W)
     per = [cpu_baseline(W, Lstar, target_s=20.0, width=args.W) for _ in range(args.steps)]
@@ -508,10 +643,10 @@ def run_reference(args):
     cpu["value"] = v
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "queries/s",
            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-           "ms_per_step": 1e3 * args.nq / v, "higher_is_better": True, "scaling": "weak",
+           "ms_per_step": 1e3 * run.nq / v, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "entry": "medoid", "L": Lstar, "k": K_NN,
-                      "recall@10": cpu["recall@10_sample"],
+           "config": {"workload": spec["desc"], "entry": "medoid", "L": Lstar, "W": args.W,
+                      "k": K_NN, "recall@10": cpu["recall@10_sample"],
                       "evals_per_query": cpu["evals_per_query"]},
            "cpu_baseline": cpu,
            "e2e": {"value": v, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

@@ -465,7 +465,7 @@ ann_status ann_medoid(const void *d_base, int64_t n, int32_t dim, int32_t dtype,
  *   medoid    in/out: the navigating node; a negative value asks for the medoid
  *   repairs   out (optional): number of edges added in step 3
  * Blocking.  ANN_ERR_CAPACITY if step 3 finds no reachable node with a free
- * slot.  Requires K <= 128, R <= min(K, 64) and dim*elem*K <= 160 KiB.
+ * slot.  Requires K <= 128 and R <= min(K, 64).
  */
 ann_status ann_build_graph(const void *d_base, int64_t n, int32_t dim, int32_t dtype, int32_t K,
                            int32_t R, float alpha, int32_t *d_graph, int32_t *medoid,

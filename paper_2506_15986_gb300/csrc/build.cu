@@ -223,7 +223,9 @@ __global__ void rescore_topk(const uint8_t *base, int rowbytes, const uint8_t *q
 // Relative-neighbourhood pruning of node p's K candidates (sorted by exact
 // (dist, id)): c is kept unless a node s kept before it has
 // alpha * delta(s, c) <= delta(p, c); at most R are kept; -1 pads the row.
-template <int DT>
+// STAGED: the K candidate rows are copied into shared memory first (when they
+// fit); otherwise they are read from global memory (L1/L2-cached) in place.
+template <int DT, bool STAGED>
 __global__ void rng_prune(const uint8_t *base, int rowbytes, int dim, int64_t n, const int32_t *cand,
                           const void *cand_d, int K, int R, float alpha, int stride, int32_t *graph)
 {
@@ -233,18 +235,25 @@ __global__ void rng_prune(const uint8_t *base, int rowbytes, int dim, int64_t n,
     if (p >= n)
         return;
     uint8_t *rows = smem;
-    int32_t *kept = reinterpret_cast<int32_t *>(smem + static_cast<size_t>(K) * stride);
-    // stage the K candidate rows
-    for (int c = 0; c < K; ++c) {
-        const int32_t id = cand[p * K + c];
-        if (id < 0)
-            continue;
-        const uint4 *src = reinterpret_cast<const uint4 *>(base + static_cast<int64_t>(id) * rowbytes);
-        uint4 *dst = reinterpret_cast<uint4 *>(rows + c * stride);
-        for (int o = lane; o < rowbytes / 16; o += 32)
-            dst[o] = src[o];
+    int32_t *kept = reinterpret_cast<int32_t *>(smem + (STAGED ? static_cast<size_t>(K) * stride : 0));
+    if constexpr (STAGED) {
+        for (int c = 0; c < K; ++c) {
+            const int32_t id = cand[p * K + c];
+            if (id < 0)
+                continue;
+            const uint4 *src = reinterpret_cast<const uint4 *>(base + static_cast<int64_t>(id) * rowbytes);
+            uint4 *dst = reinterpret_cast<uint4 *>(rows + c * stride);
+            for (int o = lane; o < rowbytes / 16; o += 32)
+                dst[o] = src[o];
+        }
+        __syncwarp();
     }
-    __syncwarp();
+    auto row = [&](int c) -> const uint8_t * {
+        if constexpr (STAGED)
+            return rows + c * stride;
+        else
+            return base + static_cast<int64_t>(cand[p * K + c]) * rowbytes;
+    };
     int nk = 0;
     for (int c = 0; c < K && nk < R; ++c) {
         const int32_t id = cand[p * K + c];
@@ -256,14 +265,14 @@ __global__ void rng_prune(const uint8_t *base, int rowbytes, int dim, int64_t n,
         else
             dpc = reinterpret_cast<const float *>(cand_d)[p * K + c];
         bool pruned = false;
-        if (lane < nk) {
-            const int s = kept[lane];
+        for (int j = lane; j < nk; j += 32) {
+            const int s = kept[j];
             float dsc;
             if constexpr (DT == ANN_U8)
-                dsc = static_cast<float>(exact_dist_bits<ANN_U8, ANN_L2>(rows + s * stride, rows + c * stride, dim));
+                dsc = static_cast<float>(exact_dist_bits<ANN_U8, ANN_L2>(row(s), row(c), dim));
             else
-                dsc = ord_to_f32(exact_dist_bits<ANN_F32, ANN_L2>(rows + s * stride, rows + c * stride, dim));
-            pruned = alpha * dsc <= dpc;
+                dsc = ord_to_f32(exact_dist_bits<ANN_F32, ANN_L2>(row(s), row(c), dim));
+            pruned |= alpha * dsc <= dpc;
         }
         if (!__any_sync(kFull, pruned)) {
             if (lane == 0)
@@ -572,16 +581,26 @@ ann_status build_graph_gpu(const void *d_base, int64_t n, int dim, int dtype, in
     if ((s16 & 1) == 0)
         s16 += 1;
     const int stride = s16 * 16;
-    const size_t smem = static_cast<size_t>(K) * stride + 4 * 64;
-    if (dtype == ANN_U8) {
-        CK(cudaFuncSetAttribute(rng_prune<ANN_U8>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
-        rng_prune<ANN_U8><<<static_cast<unsigned>(n), 32, smem, s>>>(static_cast<const uint8_t *>(d_base), rowbytes,
-                                                                    dim, n, cids.p, cd.p, K, R, alpha, stride, d_graph);
-    } else {
-        CK(cudaFuncSetAttribute(rng_prune<ANN_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
-        rng_prune<ANN_F32><<<static_cast<unsigned>(n), 32, smem, s>>>(static_cast<const uint8_t *>(d_base), rowbytes,
-                                                                     dim, n, cids.p, cd.p, K, R, alpha, stride, d_graph);
-    }
+    const bool staged = static_cast<size_t>(K) * stride <= 64 * 1024;
+    const size_t smem = (staged ? static_cast<size_t>(K) * stride : 0) + 4 * 64;
+    const uint8_t *bb = static_cast<const uint8_t *>(d_base);
+    const unsigned grid = static_cast<unsigned>(n);
+#define PRUNE(DT, ST)                                                                                          \
+    do {                                                                                                       \
+        CK(cudaFuncSetAttribute(rng_prune<DT, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,               \
+                                static_cast<int>(smem)));                                                      \
+        rng_prune<DT, ST><<<grid, 32, smem, s>>>(bb, rowbytes, dim, n, cids.p, cd.p, K, R, alpha, stride,      \
+                                                 d_graph);                                                     \
+    } while (0)
+    if (dtype == ANN_U8 && staged)
+        PRUNE(ANN_U8, true);
+    else if (dtype == ANN_U8)
+        PRUNE(ANN_U8, false);
+    else if (staged)
+        PRUNE(ANN_F32, true);
+    else
+        PRUNE(ANN_F32, false);
+#undef PRUNE
     CK(cudaGetLastError());
     // 3. navigating node
     if (*medoid < 0) {
@@ -724,7 +743,7 @@ ann_status ann_build_graph(const void *d_base, int64_t n, int32_t dim, int32_t d
         return ANN_ERR_INVALID_ARG;
     if (dtype != ANN_U8 && dtype != ANN_F32)
         return ANN_ERR_UNSUPPORTED;
-    if ((static_cast<int64_t>(dim) * es) % 16 != 0 || static_cast<int64_t>(dim) * es * K > 160 * 1024 ||
+    if ((static_cast<int64_t>(dim) * es) % 16 != 0 ||
         (reinterpret_cast<uintptr_t>(d_base) & 15) || *medoid >= n)
         return ANN_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
