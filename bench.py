@@ -11,9 +11,9 @@ entry model (Adam, batch 8,192).
 
 One step = one batch of the evaluation queries through the public path:
 ann_select_entry (query tower, then the hub-graph search or the exhaustive
-tensor-core hub scoring, whichever is faster) then ann_search_batch (W = 2
-pool entries expanded per step when the degree allows, visited-table and
-gather sizes picked by ann_autotune), at the pool size L* that first reaches
+tensor-core hub scoring, whichever is faster) then ann_search_batch (W = 4
+pool entries expanded per step, fewer when W * R would pass 128 candidates;
+visited-table, gather and distance-team sizes picked by ann_autotune), at the pool size L* that first reaches
 recall@10 >= 0.95 in the L sweep.  `value` is the learned-entry QPS; the
 medoid-entry numbers (same W, own L* and tuning) sit beside it in `config`.
 Inputs are resident in HBM when the timed region starts; every base set is
@@ -80,6 +80,13 @@ WORKLOADS = {
               "RNG prune R=32, medoid entry, L=64, k=10"),
         gen="small_u8", n=10_000, nq=100, n_train=0, dim=128, R=32, metric="l2", dtype="u8",
         hubs=0, learned=False, targets=[0.0], fixed_L=64),
+    "batch": dict(
+        desc=("batch_f32 (scaled from 10M to 2M base rows so that the exact-kNN graph builds in "
+              "seconds): N=2,000,000 fp32 d=96 (10,000-component mixture), 100,000 queries, half "
+              "shifted, per-query k in {1,10,100} and L uniform in [max(32,k),512], one persistent "
+              "launch; per-batch latency over batches of 1,000"),
+        gen="batch_f32", n=2_000_000, nq=100_000, n_train=0, dim=96, R=32, metric="l2",
+        dtype="f32", hubs=0, learned=False, targets=[0.95], batching=True),
 }
 
 
@@ -101,7 +108,7 @@ def parse():
     ap.add_argument("--l-hub", type=int, default=32)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
-    ap.add_argument("--W", type=int, default=2, help="pool entries expanded per search step")
+    ap.add_argument("--W", type=int, default=4, help="pool entries expanded per search step")
     ap.add_argument("--no-tune", action="store_true", help="skip ann_autotune at L*")
     ap.add_argument("--fixed-L", type=int, default=0,
                     help="skip the L sweep and run every entry mode at this pool size")
@@ -121,8 +128,8 @@ def parse():
         spec["n_train"] = 0
     if args.fixed_L:
         spec["fixed_L"] = args.fixed_L
-    # W * R may not exceed 64 candidates per step
-    args.W = max(1, min(args.W, 64 // spec["R"]))
+    # W * R may not exceed 128 candidates per step
+    args.W = max(1, min(args.W, 128 // spec["R"]))
     args.spec = spec
     return args
 
@@ -210,6 +217,8 @@ def generate(spec, synth):
         return synth.ip_f32(n=spec["n"], nq=spec["nq"], n_train=spec["n_train"])
     if g == "highdim_f32":
         return synth.highdim_f32(n=spec["n"], nq=spec["nq"])
+    if g == "batch_f32":
+        return synth.batch_f32(n=spec["n"], nq=spec["nq"])
     return synth.small_u8(n=spec["n"], nq=spec["nq"])
 
 
@@ -230,7 +239,7 @@ def build_workload(args, torch, ann, synth, dev):
     t_build = time.time() - t0
     q = torch.from_numpy(w["queries"]).to(dev)
     nq = q.shape[0]
-    kmax = 100 if spec.get("precision") else K_NN
+    kmax = 100 if (spec.get("precision") or spec.get("batching")) else K_NN
     gt = torch.empty((nq, kmax), dtype=torch.int32, device=dev)
     gtd = torch.empty((nq, kmax), dtype=torch.int32 if dt == ann.U8 else torch.float32, device=dev)
     ann.ann_knn(base, n, dim, dt, metric, q, nq, kmax, gt, gtd)
@@ -333,7 +342,8 @@ class Runner:
         best, ms = self.ann.ann_autotune(self.h, q, self.nq, e, self.params(L), self.ids,
                                          self.dists, 3, self.stream)
         self.tuned[L] = best
-        return {"hash_bits": best.hash_bits, "stage_rows": best.stage_rows, "search_ms": ms}
+        return {"hash_bits": best.hash_bits, "stage_rows": best.stage_rows, "team": best.team,
+                "search_ms": ms}
 
     def select(self, q):
         if self.mode == "medoid":
@@ -533,6 +543,74 @@ def precision_report(W, torch, ann, args, dev):
     return out
 
 
+def batch_report(W, torch, ann, args, dev):
+    """Mixed per-query k and L in one persistent launch over the whole stream
+    (QPS, recall@k_i), then per-batch latency over consecutive batches of
+    1,000 queries, by direct calls and through a CUDA-graph plan (p50/p99)."""
+    kq = torch.from_numpy(W["w"]["k"]).to(dev)
+    Lq = torch.from_numpy(W["w"]["L"]).to(dev)
+    q = W["q"]
+    nq = q.shape[0]
+    ids = torch.empty((nq, 100), dtype=torch.int32, device=dev)
+    dd = torch.empty((nq, 100), dtype=torch.float32, device=dev)
+    st = torch.empty((nq, 2), dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+    p = ann.search_params(100, 512, W=1, d_k=kq, d_L=Lq)
+    best, _ = ann.ann_autotune(W["h"], q, nq, None, p, ids, dd, 2, stream)
+    best.d_k, best.d_L = p.d_k, p.d_L
+    ann.ann_search_batch(W["h"], q, nq, None, best, ids, dd, st, stream)
+    if ann.ann_sync_status(W["h"], stream) != ann.OK:
+        raise RuntimeError("batched search reported a device error")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(3):
+        ann.ann_search_batch(W["h"], q, nq, None, best, ids, dd, None, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    qps = nq * 3 / (e0.elapsed_time(e1) / 1e3)
+    I = ids.cpu().numpy()
+    kk = W["w"]["k"]
+    hits = sum(len(np.intersect1d(I[i, :kk[i]], W["gt"][i, :kk[i]])) for i in range(nq))
+    rec = hits / float(kk.sum())
+    s = st.cpu().numpy()
+    # per-batch latency
+    B = 1000
+    lat, lat_plan = [], []
+    for b0 in range(0, nq, B):
+        sl = slice(b0, b0 + B)
+        pb = ann.search_params(100, 512, W=1, hash_bits=best.hash_bits, stage_rows=best.stage_rows,
+                               team=best.team, d_k=kq[sl], d_L=Lq[sl])
+        a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ann.ann_search_batch(W["h"], q[sl], B, None, pb, ids[sl], dd[sl], None, stream)
+        c.record(stream)
+        c.synchronize()
+        lat.append(a.elapsed_time(c))
+    qb, kb, lb = q[:B].clone(), kq[:B].clone(), Lq[:B].clone()
+    ib = torch.empty((B, 100), dtype=torch.int32, device=dev)
+    db = torch.empty((B, 100), dtype=torch.float32, device=dev)
+    pp = ann.search_params(100, 512, W=1, hash_bits=best.hash_bits, stage_rows=best.stage_rows,
+                           team=best.team, d_k=kb, d_L=lb)
+    plan = ann.ann_plan_create(W["h"], qb, B, ann.ENTRY_MEDOID, 0, pp, None, ib, db)
+    try:
+        for _ in range(100):
+            a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ann.ann_plan_launch(plan, stream)
+            c.record(stream)
+            c.synchronize()
+            lat_plan.append(a.elapsed_time(c))
+    finally:
+        ann.ann_plan_free(plan)
+    return {"qps_one_launch": qps, "recall_at_own_k": rec, "queries": nq,
+            "evals_per_query": float(s[:, 0].mean()), "hops_per_query": float(s[:, 1].mean()),
+            "tuned": {"hash_bits": best.hash_bits, "stage_rows": best.stage_rows, "team": best.team},
+            "batch": B, "batch_latency_ms": {"p50": float(np.percentile(lat, 50)),
+                                             "p99": float(np.percentile(lat, 99))},
+            "plan_latency_ms": {"p50": float(np.percentile(lat_plan, 50)),
+                                "p99": float(np.percentile(lat_plan, 99))}}
+
+
 def run_gpu(args):
     import torch
     from paper_2506_15986_gb300 import _build, ann, synth
@@ -577,6 +655,7 @@ def run_gpu(args):
     e2e = end_to_end(R["run"], torch, R["L"], max(10, args.steps // 4))
     e2e["value"] *= world
     prec = precision_report(W, torch, ann, args, dev) if spec.get("precision") else None
+    batching = batch_report(W, torch, ann, args, dev) if spec.get("batching") else None
     peak, peak_kind = peaks()
     achieved = R["alg_bytes"] / (search_ms / 1e3) / 1e9
     out = None
@@ -592,7 +671,7 @@ def run_gpu(args):
                "l2": "inputs larger than L2 (129 MB), no flush" if big
                else "base smaller than L2: an L2-resident parity config",
                "graph_build_s": W["t_build"], "repairs": W["repairs"], "learned": learned,
-               "precision": prec, "parallelism": f"replicas{world}"}
+               "precision": prec, "batching": batching, "parallelism": f"replicas{world}"}
         if "medoid" in others:
             med = others["medoid"]
             cfg["learned_vs_medoid"] = {

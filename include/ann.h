@@ -56,15 +56,15 @@ typedef struct ann_index ann_index;
 /* Limits of one search */
 #define ANN_MAX_L 512      /* pool size L */
 #define ANN_MAX_W 4        /* entries expanded per step */
-#define ANN_MAX_STEP_CAND 64 /* W * degree */
+#define ANN_MAX_STEP_CAND 128 /* W * degree */
 
 /*
  * Index description for ann_index_create.  The path searches a fixed-degree
  * proximity graph (Sec. 2.1, Def. 1) over base vectors D.
  *   n, dim       number of base vectors and their dimension; dim * element
  *                size must be a multiple of 16 bytes (16-byte row gathers)
- *   degree       R, slots per adjacency row (R * ANN_MAX_W is capped by
- *                ANN_MAX_STEP_CAND for W > 1)
+ *   degree       R, slots per adjacency row, 1..ANN_MAX_STEP_CAND (a search
+ *                expanding W entries per step needs W * R <= ANN_MAX_STEP_CAND)
  *   dtype,metric see ann_dtype / ann_metric; uint8 supports ANN_L2 only
  *   base         n*dim elements of dtype, row-major (host or device pointer)
  *   graph        n*degree int32 node ids, row-major; -1 marks an unused
@@ -93,12 +93,17 @@ typedef struct {
  *   k         results per query, 1 <= k <= L; also the row stride of the
  *             outputs when d_k is given (then every d_k[i] <= k)
  *   L         pool size, 1 <= L <= ANN_MAX_L; the maximum when d_L is given
- *   W         pool entries expanded per step, 1..ANN_MAX_W, W*degree <= 64
+ *   W         pool entries expanded per step, 1..ANN_MAX_W, W*degree <= 128
  *   hash_bits log2 of the per-query shared-memory visited-table capacity,
  *             0 = chosen from L; 8..15
  *   stage_rows neighbour rows gathered into shared memory per round, 0 =
  *             chosen from the row size; 1..32.  hash_bits and stage_rows change
  *             speed only, never results (see ann_autotune)
+ *   team      lanes that compute one distance together (the warp evaluates
+ *             32/team staged rows at a time), 0 = chosen from the row size;
+ *             1, 2, 4, 8, 16 or 32.  Speed only for uint8 data; for float
+ *             data it sets the FP32 summation order, so distances may differ
+ *             in the last bits between teams
  *   flags     ANN_SEARCH_* bits.  ANN_SEARCH_RERANK: after the search, every
  *             id of the final pool (L entries) is re-scored exactly from the
  *             index's fp32 copy of the rows (ann_index_desc.base_f32; without
@@ -117,6 +122,7 @@ typedef struct {
     int32_t W;
     int32_t hash_bits;
     int32_t stage_rows;
+    int32_t team;
     uint32_t flags;
     const int32_t *d_k;
     const int32_t *d_L;
@@ -211,11 +217,13 @@ ann_status ann_plan_free(ann_plan *plan);
 
 /*
  * Time ann_search_batch over the given batch for visited-table sizes around
- * and below the default (hash_bits) and gather round sizes (stage_rows 4, 8, 16), reps
- * runs each after one warm-up, and return in *best the copy of *p with the
- * fastest pair (*best_ms: its mean time).  Both knobs change speed only: the
- * visited set stays exact (shared table plus global spill) and the gather
- * order does not enter any result.  Blocking; d_ids / d_dists receive the
+ * and below the default (hash_bits), gather round sizes (stage_rows 4, 8, 16)
+ * and distance team sizes (team 4, 8, 16, 32 where a team has at least one
+ * 16-byte chunk of the row per lane), reps runs each after one warm-up, and
+ * return in *best the copy of *p with the fastest combination (*best_ms: its
+ * mean time).  The visited set stays exact (shared table plus global spill)
+ * and the gather order does not enter any result; the team size only moves
+ * float distances by FP32 rounding.  Blocking; d_ids / d_dists receive the
  * results of the last run.
  */
 ann_status ann_autotune(ann_index *idx, const void *d_queries, int64_t nq, const int32_t *d_entry,

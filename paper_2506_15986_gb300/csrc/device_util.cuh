@@ -157,6 +157,22 @@ __device__ __forceinline__ uint64_t warp_sort32(uint64_t k, int lane)
     return k;
 }
 
+// Keys of lanes [0, width) sorted ascending (width a power of two <= 32);
+// lanes at or above width exchange only among themselves.  The whole warp
+// must call it.
+__device__ __forceinline__ uint64_t warp_sort_lanes(uint64_t k, int lane, int width)
+{
+    for (int kk = 2; kk <= width; kk <<= 1) {
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            const uint64_t o = __shfl_xor_sync(kFull, k, j);
+            const bool lower = (lane & j) == 0;
+            const bool asc = (lane & kk) == 0;
+            k = (lower == asc) ? kmin(k, o) : kmax(k, o);
+        }
+    }
+    return k;
+}
+
 // 64 keys, two per lane: element lane in k0, element lane+32 in k1.
 __device__ __forceinline__ void warp_sort64(uint64_t &k0, uint64_t &k1, int lane)
 {

@@ -481,7 +481,10 @@ ann_status build_hub_index(ann_index *idx, ann_entry_model *m, const int32_t *hu
     d.graph = m->hub_graph;
     d.medoid = m->hub_entry;
     d.base_f32 = nullptr;
-    return ann_index_create(&d, idx->device, &m->hub_index);
+    ann_status st = ann_index_create(&d, idx->device, &m->hub_index);
+    if (st == ANN_OK)
+        m->hub_index->status_sink = idx->d_status;  // hub-graph search errors reach the parent's status
+    return st;
 }
 
 }  // namespace ann

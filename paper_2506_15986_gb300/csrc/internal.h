@@ -22,6 +22,7 @@ struct ann_index {
     int32_t *d_graph = nullptr;
     float *d_base_f32 = nullptr;  // optional exact copy for rerank
     int *d_status = nullptr;      // device status word (kStatus* bits)
+    int *status_sink = nullptr;   // if set, kernels report here instead (hub index -> its parent)
     cudaMemPool_t pool = nullptr; // stream-ordered scratch
     ann_entry_model *model = nullptr;
 };
@@ -60,6 +61,10 @@ struct SearchLaunch {
 
 // Queues the beam-search kernel (search.cu).
 ann_status launch_search(ann_index *idx, const SearchLaunch &L, cudaStream_t s);
+
+// Lanes per distance when ann_search_params.team is 0: the smallest power of
+// two >= 4 that leaves each lane at most four 16-byte chunks of a row.
+int default_team(int rowbytes);
 
 // Scratch bytes launch_search needs for `teams` teams at the given params.
 size_t search_scratch_bytes(int teams, int spill_bits);

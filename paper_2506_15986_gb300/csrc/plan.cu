@@ -116,38 +116,57 @@ ann_status ann_autotune(ann_index *idx, const void *d_queries, int64_t nq, const
     float bms = 1e30f;
     ann_search_params bp = *p;
     ann_status st = ANN_OK;
+    // times one candidate; false on a hard error (st set)
+    auto trial = [&](const ann_search_params &c) -> bool {
+        st = ann_search_batch(idx, d_queries, nq, d_entry, &c, d_ids, d_dists, nullptr, s);  // warm-up
+        if (st == ANN_ERR_UNSUPPORTED) {  // does not fit in shared memory
+            st = ANN_OK;
+            return true;
+        }
+        if (st != ANN_OK)
+            return false;
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < reps && st == ANN_OK; ++r)
+            st = ann_search_batch(idx, d_queries, nq, d_entry, &c, d_ids, d_dists, nullptr, s);
+        cudaEventRecord(e1, s);
+        if (st != ANN_OK)
+            return false;
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            st = ANN_ERR_CUDA;
+            return false;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= reps;
+        if (ms < bms) {
+            bms = ms;
+            bp = c;
+        }
+        return true;
+    };
+    // stage 1: visited-table size x gather round size at the given team size
+    bool ok = true;
     for (int hb : hbs) {
         for (int sr : srs) {
             ann_search_params c = *p;
             c.hash_bits = hb;
             c.stage_rows = sr;
-            st = ann_search_batch(idx, d_queries, nq, d_entry, &c, d_ids, d_dists, nullptr, s);  // warm-up
-            if (st == ANN_ERR_UNSUPPORTED) {  // does not fit in shared memory
-                st = ANN_OK;
-                continue;
-            }
-            if (st != ANN_OK)
+            c.team = p->team > 0 ? p->team : ann::default_team(idx->rowbytes);
+            if (!(ok = trial(c)))
                 break;
-            cudaEventRecord(e0, s);
-            for (int r = 0; r < reps && st == ANN_OK; ++r)
-                st = ann_search_batch(idx, d_queries, nq, d_entry, &c, d_ids, d_dists, nullptr, s);
-            cudaEventRecord(e1, s);
-            if (st != ANN_OK)
-                break;
-            if (cudaEventSynchronize(e1) != cudaSuccess) {
-                st = ANN_ERR_CUDA;
-                break;
-            }
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            ms /= reps;
-            if (ms < bms) {
-                bms = ms;
-                bp = c;
-            }
         }
-        if (st != ANN_OK)
+        if (!ok)
             break;
+    }
+    // stage 2: team sizes at the best pair, from 1 to 16 chunks of the row per lane
+    const int chunks = idx->rowbytes / 16;
+    const ann_search_params b1 = bp;
+    for (int g = 2; ok && g <= 32; g <<= 1) {
+        if (g > chunks || g * 16 < chunks || g == b1.team)
+            continue;
+        ann_search_params c = b1;
+        c.team = g;
+        ok = trial(c);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

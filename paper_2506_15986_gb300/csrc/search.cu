@@ -12,9 +12,10 @@
 //     new candidates are sorted by a warp-shuffle bitonic network and merged
 //     in by rank (merge path);
 //   - the visited set: an open-addressing hash table (linear probing, key
-//     id+1, 0 = empty).  When it would pass 3/4 load, later inserts go to a
-//     per-team table in global scratch, so the set stays exact; when that
-//     one would pass 3/4 load the query fails with a capacity status.
+//     id+1, 0 = empty).  When it would pass 3/4 load, its entries move to a
+//     per-team table in global scratch that takes every later insert, so
+//     the set stays exact; when that one would pass 3/4 load the query fails
+//     with a capacity status.
 // Semantics follow the sorted-pool reading of Algorithm 1: single entry, a
 // node is visited when its distance is computed, a step expands the first W
 // unexpanded pool entries, the pool is truncated to L, the search stops when
@@ -35,6 +36,7 @@ namespace {
 
 constexpr int kSearchWarps = 1;  // warps (teams) per CTA
 constexpr int kTimeoutIters = 1 << 22;
+constexpr int kSlots = ANN_MAX_STEP_CAND / 32;  // neighbour slots per lane in one step
 
 struct SearchArgs {
     const uint8_t *base;
@@ -60,6 +62,7 @@ struct SearchArgs {
     // per-warp shared-memory layout (byte offsets)
     int off_sel, off_q, off_stage, off_pool, off_ptmp, off_cbuf, off_cids, off_hash, per_warp;
     int stage_rows, stage_stride;
+    int team_lg;  // log2 of the lanes computing one distance
 };
 
 __device__ __forceinline__ uint32_t hash_slot(uint32_t key, int bits)
@@ -87,15 +90,7 @@ __device__ __forceinline__ int visit(uint32_t *htab, int hbits, bool global_mode
         }
         return -1;
     }
-    // shared table is frozen in global mode: lookup only
-    for (uint32_t p = 0; p <= hmask; ++p) {
-        uint32_t v = htab[h];
-        if (v == key)
-            return 0;
-        if (v == 0u)
-            break;
-        h = (h + 1u) & hmask;
-    }
+    // global mode: the shared table's entries were moved to the global table
     const uint32_t gmask = (1u << gbits) - 1u;
     uint32_t g = hash_slot(key, gbits);
     for (uint32_t p = 0; p <= gmask; ++p) {
@@ -109,19 +104,60 @@ __device__ __forceinline__ int visit(uint32_t *htab, int hbits, bool global_mode
     return -1;
 }
 
-// Distance of one staged row to the query, computed by a group of 8 lanes
-// (sub = lane % 8 takes the row's 16-byte chunks sub, sub+8, ...) and
-// combined with three xor-shuffles inside the group; every lane of the group
-// returns the order-preserving key bits.  The whole warp must call it.
+// Visited test-and-insert for NS ids per lane (-1 = none) in one table.
+// res[s] = 1 when ids[s] was not yet visited (and is now), 0 when it was, -1
+// when the table is full.  All first probes go out before the collision
+// chains are followed, so their latencies overlap.  Concurrent inserts of the
+// same id (from any lane or slot) give exactly one 1.
+template <int NS>
+__device__ __forceinline__ void visit_slots(uint32_t *tab, int bits, const int32_t (&ids)[NS], int (&res)[NS])
+{
+    const uint32_t mask = (1u << bits) - 1u;
+    uint32_t h[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        res[s] = 0;
+        h[s] = 0;
+        if (ids[s] >= 0) {
+            const uint32_t key = static_cast<uint32_t>(ids[s]) + 1u;
+            h[s] = hash_slot(key, bits);
+            const uint32_t old = atomicCAS(&tab[h[s]], 0u, key);
+            res[s] = old == 0u ? 1 : (old == key ? 0 : 2);
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        if (res[s] == 2) {
+            const uint32_t key = static_cast<uint32_t>(ids[s]) + 1u;
+            uint32_t g = h[s];
+            res[s] = -1;
+            for (uint32_t p = 1; p <= mask; ++p) {
+                g = (g + 1u) & mask;
+                const uint32_t old = atomicCAS(&tab[g], 0u, key);
+                if (old == 0u || old == key) {
+                    res[s] = old == 0u ? 1 : 0;
+                    break;
+                }
+            }
+        }
+    }
+}
+
+// Distance of one staged row to the query, computed by a team of G lanes
+// (G a power of two <= 32; sub = lane % G takes the row's 16-byte chunks sub,
+// sub+G, ...) and combined with log2(G) xor-shuffles inside the team; every
+// lane of the team returns the order-preserving key bits.  The whole warp
+// must call it.
 template <int DT, int MT>
-__device__ __forceinline__ uint32_t group_distance(const uint8_t *row, const uint8_t *q, int rowbytes, int sub)
+__device__ __forceinline__ uint32_t group_distance(const uint8_t *row, const uint8_t *q, int rowbytes, int sub,
+                                                   int G)
 {
     const int chunks = rowbytes / 16;
     if constexpr (DT == ANN_U8) {
         const uint4 *x4 = reinterpret_cast<const uint4 *>(row);
         const uint4 *q4 = reinterpret_cast<const uint4 *>(q);
         uint32_t acc = 0;
-        for (int c = sub; c < chunks; c += 8) {
+        for (int c = sub; c < chunks; c += G) {
             const uint4 x = x4[c], y = q4[c];
             uint32_t d;
             d = __vabsdiffu4(x.x, y.x);
@@ -133,9 +169,8 @@ __device__ __forceinline__ uint32_t group_distance(const uint8_t *row, const uin
             d = __vabsdiffu4(x.w, y.w);
             acc = __dp4a(d, d, acc);
         }
-        acc += __shfl_xor_sync(kFull, acc, 4);
-        acc += __shfl_xor_sync(kFull, acc, 2);
-        acc += __shfl_xor_sync(kFull, acc, 1);
+        for (int o = G >> 1; o > 0; o >>= 1)
+            acc += __shfl_xor_sync(kFull, acc, o);
         return acc;  // exact non-negative int32, ordered as unsigned
     } else {
         const float4 *q4 = reinterpret_cast<const float4 *>(q);
@@ -156,13 +191,13 @@ __device__ __forceinline__ uint32_t group_distance(const uint8_t *row, const uin
         };
         if constexpr (DT == ANN_F32) {
             const float4 *x4 = reinterpret_cast<const float4 *>(row);
-            for (int c = sub; c < chunks; c += 8) {
+            for (int c = sub; c < chunks; c += G) {
                 const float4 x = x4[c];
                 acc4(x.x, x.y, x.z, x.w, q4[c]);
             }
         } else {
             const uint4 *x8 = reinterpret_cast<const uint4 *>(row);
-            for (int c = sub; c < chunks; c += 8) {
+            for (int c = sub; c < chunks; c += G) {
                 const uint4 x = x8[c];
                 float2 f0, f1, f2, f3;
                 if constexpr (DT == ANN_F16) {
@@ -181,9 +216,8 @@ __device__ __forceinline__ uint32_t group_distance(const uint8_t *row, const uin
             }
         }
         float s = a0 + a1;
-        s += __shfl_xor_sync(kFull, s, 4);
-        s += __shfl_xor_sync(kFull, s, 2);
-        s += __shfl_xor_sync(kFull, s, 1);
+        for (int o = G >> 1; o > 0; o >>= 1)
+            s += __shfl_xor_sync(kFull, s, o);
         if constexpr (MT == ANN_IP)
             s = -s;
         return f32_to_ord(s);
@@ -241,9 +275,12 @@ __global__ void __launch_bounds__(32 * kSearchWarps) beam_search_kernel(const Se
         }
 
         int cnt = 0, cursor = 0, evals = 0, hops = 0, hused = 0, gused = 0;
-        int spec_n = 0;  // entries speculated by the previous step (adjacency in spec0/spec1)
-        int32_t spec0 = -1, spec1 = -1;
-        int32_t *spec_old = sel + ANN_MAX_W, *spec_new = sel + 2 * ANN_MAX_W;
+        int32_t *pred = sel + ANN_MAX_W;  // predicted ids of the next selection
+        int npred = 0;
+        int32_t nxt[kSlots];  // their adjacency rows, lane-distributed like cur[]
+#pragma unroll
+        for (int r = 0; r < kSlots; ++r)
+            nxt[r] = -1;
         bool gmode = false, found = false;
         if (!failed) {
             // query row -> shared memory; clear the visited table
@@ -265,7 +302,9 @@ __global__ void __launch_bounds__(32 * kSearchWarps) beam_search_kernel(const Se
         __syncwarp();
 
         while (!failed) {
-            // ---- evaluate the nc candidates in cids[] and merge them into the pool
+            // ---- evaluate the nc candidates in cids[]; the survivors end sorted
+            // in cbuf[0, m)
+            int m = 0;
             if (nc > 0) {
                 for (int c0 = 0; c0 < nc; c0 += a.stage_rows) {
                     const int ch = min(a.stage_rows, nc - c0);
@@ -285,12 +324,13 @@ __global__ void __launch_bounds__(32 * kSearchWarps) beam_search_kernel(const Se
                         break;
                     }
                     phase ^= 1u;
-                    // 8 lanes per staged row, 4 rows per pass
-                    for (int r0 = 0; r0 < ch; r0 += 4) {
-                        const int r = r0 + (lane >> 3);
+                    // a team of G lanes per staged row, 32 / G rows per pass
+                    for (int r0 = 0; r0 < ch; r0 += 32 >> a.team_lg) {
+                        const int r = r0 + (lane >> a.team_lg);
+                        const int sub = lane & ((1 << a.team_lg) - 1);
                         const uint32_t bits = group_distance<DT, MT>(stage + min(r, ch - 1) * a.stage_stride,
-                                                                     qbuf, a.rowbytes, lane & 7);
-                        if (r < ch && (lane & 7) == 0)
+                                                                     qbuf, a.rowbytes, sub, 1 << a.team_lg);
+                        if (r < ch && sub == 0)
                             cbuf[c0 + r] = make_key(bits, cids[c0 + r]);
                     }
                     __syncwarp();
@@ -298,109 +338,178 @@ __global__ void __launch_bounds__(32 * kSearchWarps) beam_search_kernel(const Se
                 }
                 if (failed)
                     break;
-                uint64_t k0 = lane < nc ? cbuf[lane] : kKeyMax;
-                uint64_t k1 = lane + 32 < nc ? cbuf[lane + 32] : kKeyMax;
+                // candidates no better than a full pool's last entry cannot
+                // enter it; only the survivors are sorted
                 const uint64_t worst = (cnt == Lq) ? key_plain(pool[Lq - 1]) : kKeyMax;
-                if (k0 >= worst)
-                    k0 = kKeyMax;
-                if (k1 >= worst)
-                    k1 = kKeyMax;
-                if (nc > 32)
-                    warp_sort64(k0, k1, lane);
-                else
-                    k0 = warp_sort32(k0, lane);
-                const int m = __popc(__ballot_sync(kFull, k0 != kKeyMax)) +
-                              __popc(__ballot_sync(kFull, k1 != kKeyMax));
+                uint64_t kk[kSlots];
+                unsigned bm[kSlots];
+#pragma unroll
+                for (int s = 0; s < kSlots; ++s) {
+                    uint64_t v = lane + 32 * s < nc ? cbuf[lane + 32 * s] : kKeyMax;
+                    if (v >= worst)
+                        v = kKeyMax;
+                    kk[s] = v;
+                    bm[s] = __ballot_sync(kFull, v != kKeyMax);
+                    m += __popc(bm[s]);
+                }
                 __syncwarp();
                 if (m > 0) {
-                    cbuf[lane] = k0;
-                    cbuf[lane + 32] = k1;
-                    __syncwarp();
-                    const int p0 = count_less(pool, cnt, cbuf[0]);
-                    const int mv = cnt - p0;
-                    for (int i = lane; i < mv; i += 32)
-                        ptmp[i] = pool[p0 + i];
-                    __syncwarp();
-                    for (int i = lane; i < mv; i += 32) {
-                        const uint64_t v = ptmp[i];
-                        const int np = p0 + i + count_less(cbuf, m, key_plain(v));
-                        if (np < Lq)
-                            pool[np] = v;
+                    if (m <= 32 || (m <= 64 && nc > 64)) {
+                        // compact the survivors into cbuf[0, m) (a 64-key
+                        // sort of candidates that all sit in slots 0-1 needs
+                        // none: the dropped ones sort to the end)
+                        int base = 0;
+#pragma unroll
+                        for (int s = 0; s < kSlots; ++s) {
+                            if (kk[s] != kKeyMax)
+                                cbuf[base + __popc(bm[s] & lanemask_lt())] = kk[s];
+                            base += __popc(bm[s]);
+                        }
+                        __syncwarp();
+                        kk[0] = lane < m ? cbuf[lane] : kKeyMax;
+                        kk[1] = lane + 32 < m ? cbuf[lane + 32] : kKeyMax;
+                        __syncwarp();
                     }
-                    for (int j = lane; j < m; j += 32) {
-                        const uint64_t v = cbuf[j];
-                        const int np = p0 + j + count_less(ptmp, mv, v);
-                        if (np < Lq)
-                            pool[np] = v;
+                    if (m <= 32) {
+                        // sort over the next power of two only
+                        int width = 1;
+                        while (width < m)
+                            width <<= 1;
+                        kk[0] = warp_sort_lanes(kk[0], lane, width);
+                        cbuf[lane] = kk[0];
+                    } else if (m <= 64) {
+                        warp_sort64(kk[0], kk[1], lane);
+                        cbuf[lane] = kk[0];
+                        cbuf[lane + 32] = kk[1];
+                    } else {
+                        warp_sort_n<kSlots>(kk, lane);
+#pragma unroll
+                        for (int s = 0; s < kSlots; ++s)
+                            cbuf[lane + 32 * s] = kk[s];
                     }
                     __syncwarp();
-                    cnt = min(Lq, cnt + m);
-                    cursor = min(cursor, p0);
                 }
+            }
+
+            // ---- predict the next selection: the W smallest unexpanded keys
+            // among the pool and the survivors.  Their adjacency rows are
+            // loaded now, so the loads overlap the merge.
+            {
+                int nf = 0;
+                for (int i0 = cursor; i0 < cnt && nf < a.W; i0 += 32) {
+                    const int i = i0 + lane;
+                    const bool un = i < cnt && !(pool[i] & 1ull);
+                    const unsigned um = __ballot_sync(kFull, un);
+                    const int g = nf + __popc(um & lanemask_lt());
+                    if (un && g < a.W)
+                        ptmp[g] = pool[i];  // ptmp is free until the merge
+                    nf = min(a.W, nf + __popc(um));
+                }
+                __syncwarp();
+                const int mw = min(m, a.W);
+                int i = 0, j = 0, np = 0;
+                for (; np < a.W && (i < nf || j < mw); ++np) {
+                    const bool from_pool = j >= mw || (i < nf && ptmp[i] < cbuf[j]);
+                    const uint64_t v = from_pool ? ptmp[i++] : cbuf[j++];
+                    if (lane == 0)
+                        pred[np] = key_id(v);
+                }
+                npred = np;
+                __syncwarp();
+                const int tp = npred * a.R;
+#pragma unroll
+                for (int r = 0; r < kSlots; ++r) {
+                    const int t = lane + 32 * r;
+                    nxt[r] = t < tp ? __ldg(a.graph + static_cast<int64_t>(pred[t / a.R]) * a.R + t % a.R) : -1;
+                }
+            }
+
+            // ---- merge the survivors into the pool by rank
+            if (m > 0) {
+                const int p0 = count_less(pool, cnt, cbuf[0]);
+                const int mv = cnt - p0;
+                for (int i = lane; i < mv; i += 32)
+                    ptmp[i] = pool[p0 + i];
+                __syncwarp();
+                for (int i = lane; i < mv; i += 32) {
+                    const uint64_t v = ptmp[i];
+                    const int np = p0 + i + count_less(cbuf, m, key_plain(v));
+                    if (np < Lq)
+                        pool[np] = v;
+                }
+                for (int j = lane; j < m; j += 32) {
+                    const uint64_t v = cbuf[j];
+                    const int np = p0 + j + count_less(ptmp, mv, v);
+                    if (np < Lq)
+                        pool[np] = v;
+                }
+                __syncwarp();
+                cnt = min(Lq, cnt + m);
+                cursor = min(cursor, p0);
             }
             if (found)
                 break;
 
-            // ---- select the first W unexpanded pool entries (marked expanded)
-            // and the W after them (not marked: they are usually the next
-            // step's choice, so their adjacency rows are fetched one step ahead)
-            int nf = 0, first = -1;
-            for (int i0 = cursor; i0 < cnt && nf < 2 * a.W; i0 += 32) {
+            // ---- select the first W unexpanded pool entries; mark them expanded
+            int ns = 0, first = -1;
+            for (int i0 = cursor; i0 < cnt && ns < a.W; i0 += 32) {
                 const int i = i0 + lane;
                 const bool un = i < cnt && !(pool[i] & 1ull);
                 const unsigned um = __ballot_sync(kFull, un);
                 if (um) {
                     if (first < 0)
                         first = i0 + __ffs(um) - 1;
-                    const int g = nf + __popc(um & lanemask_lt());
+                    const int g = ns + __popc(um & lanemask_lt());
                     if (un && g < a.W) {
                         const uint64_t v = pool[i];
                         pool[i] = v | 1ull;
                         sel[g] = key_id(v);
-                    } else if (un && g < 2 * a.W) {
-                        spec_new[g - a.W] = key_id(pool[i]);
                     }
-                    nf = min(2 * a.W, nf + __popc(um));
+                    ns = min(a.W, ns + __popc(um));
                 }
             }
             __syncwarp();
-            const int ns = min(nf, a.W);
             if (ns == 0)
                 break;
             cursor = first;
             hops += ns;
 
-            // ---- adjacency rows of the selected entries: taken from last step's
-            // speculative fetch when it named the same entries, else loaded now
+            // ---- adjacency rows of the selected entries: the predicted ones,
+            // unless truncation to L dropped a predicted entry (then loaded now)
             const int total = ns * a.R;
-            bool hit = ns == spec_n;
+            bool hit = ns == npred;
             for (int s = 0; s < ns && hit; ++s)
-                hit = sel[s] == spec_old[s];
-            int32_t cur0 = spec0, cur1 = spec1;
-            if (!hit) {
-                cur0 = lane < total ? __ldg(a.graph + static_cast<int64_t>(sel[lane / a.R]) * a.R + lane % a.R) : -1;
-                cur1 = lane + 32 < total
-                           ? __ldg(a.graph + static_cast<int64_t>(sel[(lane + 32) / a.R]) * a.R + (lane + 32) % a.R)
-                           : -1;
-            }
-            spec_n = nf - ns;
-            {
-                const int tsp = spec_n * a.R;
-                spec0 = lane < tsp ? __ldg(a.graph + static_cast<int64_t>(spec_new[lane / a.R]) * a.R + lane % a.R)
-                                   : -1;
-                spec1 = lane + 32 < tsp ? __ldg(a.graph + static_cast<int64_t>(spec_new[(lane + 32) / a.R]) * a.R +
-                                                (lane + 32) % a.R)
-                                        : -1;
-                int32_t *t = spec_old;
-                spec_old = spec_new;
-                spec_new = t;
+                hit = sel[s] == pred[s];
+            int32_t cur[kSlots];
+#pragma unroll
+            for (int r = 0; r < kSlots; ++r) {
+                const int t = lane + 32 * r;
+                cur[r] = hit ? nxt[r]
+                             : (t < total ? __ldg(a.graph + static_cast<int64_t>(sel[t / a.R]) * a.R + t % a.R) : -1);
             }
 
             // ---- neighbours of the selected entries: visited test, compaction
             if (!gmode && hused + total > hlimit) {
-                gmode = true;  // freeze the shared table, continue in global scratch
+                // continue in the global table: clear it, then move the shared
+                // table's entries into it so that every later lookup probes
+                // one table only
+                gmode = true;
                 for (int o = lane; o < (1 << a.spill_bits) / 4; o += 32)
                     reinterpret_cast<uint4 *>(gtab)[o] = make_uint4(0u, 0u, 0u, 0u);
+                __syncwarp();
+                const uint32_t gmask = (1u << a.spill_bits) - 1u;
+                for (int o = lane; o < hcap; o += 32) {
+                    const uint32_t key = htab[o];
+                    if (key == 0u)
+                        continue;
+                    uint32_t g = hash_slot(key, a.spill_bits);
+                    for (uint32_t pr = 0; pr <= gmask; ++pr) {
+                        if (atomicCAS(&gtab[g], 0u, key) == 0u)
+                            break;
+                        g = (g + 1u) & gmask;
+                    }
+                }
+                gused = hused;
                 __syncwarp();
             }
             if (gmode && gused + total > glimit) {
@@ -409,19 +518,30 @@ __global__ void __launch_bounds__(32 * kSearchWarps) beam_search_kernel(const Se
                     atomicOr(a.status, kStatusCapacityBit);
                 break;
             }
+            // every slot's first probe is issued before any result is used, so
+            // their latencies overlap (global atomics in spill mode)
+            int32_t vid[kSlots];
+            int res[kSlots];
+#pragma unroll
+            for (int s = 0; s < kSlots; ++s) {
+                const int32_t id = lane + 32 * s < total ? cur[s] : -1;
+                vid[s] = (id >= 0 && id < a.n) ? id : -1;
+            }
+            if (gmode)
+                visit_slots<kSlots>(gtab, a.spill_bits, vid, res);
+            else
+                visit_slots<kSlots>(htab, a.hash_bits, vid, res);
             nc = 0;
             bool bad = false;
-            for (int t0 = 0; t0 < total; t0 += 32) {
-                const int t = t0 + lane;
-                const int32_t id = t < total ? (t0 == 0 ? cur0 : cur1) : -1;
-                int r = 0;
-                if (id >= 0 && id < a.n)
-                    r = visit(htab, a.hash_bits, gmode, gtab, a.spill_bits, id);
-                bad |= (r < 0);
-                const unsigned nm = __ballot_sync(kFull, r == 1);
-                if (r == 1) {
-                    cids[nc + __popc(nm & lanemask_lt())] = id;
-                    if (id == target)
+#pragma unroll
+            for (int s = 0; s < kSlots; ++s) {
+                if (32 * s >= total)
+                    break;
+                bad |= (res[s] < 0);
+                const unsigned nm = __ballot_sync(kFull, res[s] == 1);
+                if (res[s] == 1) {
+                    cids[nc + __popc(nm & lanemask_lt())] = vid[s];
+                    if (vid[s] == target)
                         found = true;
                 }
                 nc += __popc(nm);
@@ -586,6 +706,15 @@ ann_status launch_typed(const SearchArgs &a, size_t smem, int teams, cudaStream_
 
 }  // namespace
 
+int default_team(int rowbytes)
+{
+    const int chunks = rowbytes / 16;
+    int G = 4;
+    while (G < 32 && chunks > 4 * G)
+        G <<= 1;
+    return G;
+}
+
 size_t search_scratch_bytes(int teams, int spill_bits)
 {
     return 256 + static_cast<size_t>(teams) * (static_cast<size_t>(4) << spill_bits);
@@ -616,7 +745,7 @@ ann_status launch_search(ann_index *idx, const SearchLaunch &L, cudaStream_t s)
     a.out_ids = L.ids;
     a.out_dists = L.dists;
     a.out_stats = L.stats;
-    a.status = idx->d_status;
+    a.status = idx->status_sink ? idx->status_sink : idx->d_status;
 
     int hb = p->hash_bits;
     if (hb == 0) {
@@ -637,9 +766,20 @@ ann_status launch_search(ann_index *idx, const SearchLaunch &L, cudaStream_t s)
     a.spill_bits = sb;
 
     const int maxc = p->W * idx->degree;
-    int s16 = idx->rowbytes / 16;
-    if ((s16 & 1) == 0)
-        s16 += 1;  // odd 16-byte stride: 8-lane phases of 16-byte loads hit distinct banks
+    // distance team: the smallest power of two >= 4 that leaves at most four
+    // 16-byte chunks of a row to each lane, unless the caller fixed it
+    const int chunks = idx->rowbytes / 16;
+    const int G = p->team > 0 ? p->team : default_team(idx->rowbytes);
+    a.team_lg = 0;
+    while ((1 << a.team_lg) < G)
+        ++a.team_lg;
+    // staging stride in 16-byte units.  A quarter-warp phase of 16-byte loads
+    // covers 8 lanes; with G < 8 they read 8 / G rows, whose G-chunk runs hit
+    // distinct banks when the stride is G times an odd number.
+    int s16 = chunks;
+    if (G < 8)
+        while (s16 % G != 0 || ((s16 / G) & 1) == 0)
+            ++s16;
     a.stage_stride = s16 * 16;
     // Most steps find far fewer new neighbours than W * R (about 9 of 32 on
     // average), so 16 rows per gather round keep shared memory per team small
@@ -649,7 +789,7 @@ ann_status launch_search(ann_index *idx, const SearchLaunch &L, cudaStream_t s)
 
     size_t off = 16;  // mbarrier
     a.off_sel = static_cast<int>(off);
-    off = align_up(off + 4 * 3 * ANN_MAX_W, 16);  // selected + two speculated sets
+    off = align_up(off + 4 * 2 * ANN_MAX_W, 16);  // selected and predicted ids
     a.off_q = static_cast<int>(off);
     off = align_up(off + L.qbytes, 16);
     a.off_stage = static_cast<int>(off);

@@ -101,6 +101,19 @@ def test_autotune_keeps_results(case):
     ref = ids.clone(), dd.clone()
     best, ms = ann.ann_autotune(case["h"], q, nq, None, p, ids, dd, reps=2)
     assert ms > 0 and best.hash_bits >= 8 and best.stage_rows in (4, 8, 16)
+    assert best.team in (2, 4, 8, 16, 32)
     ann.ann_search_batch(case["h"], q, nq, None, best, ids, dd)
     torch.cuda.synchronize()
-    assert torch.equal(ids, ref[0]) and torch.equal(dd, ref[1])
+    # the visited-table and gather sizes never change results: equal to a
+    # run with the default knobs at the same team size
+    same = ann.search_params(10, 128, team=best.team)
+    ids2, dd2 = torch.empty_like(ids), torch.empty_like(dd)
+    ann.ann_search_batch(case["h"], q, nq, None, same, ids2, dd2)
+    torch.cuda.synchronize()
+    assert torch.equal(ids, ids2) and torch.equal(dd, dd2)
+    # another team size only reorders the FP32 sums: the fp32 parity bar
+    a, b = ids.cpu().numpy(), ref[0].cpu().numpy()
+    assert (a == b).mean() >= 0.999
+    ok = a == b
+    da, db = dd.cpu().numpy()[ok].astype(np.float64), ref[1].cpu().numpy()[ok].astype(np.float64)
+    assert (np.abs(da - db) <= 1e-5 * np.abs(db)).all()

@@ -66,7 +66,8 @@ def test_toy_graphs_exact(golden_dir):
         assert (int(ev[0]), int(hp[0])) == (c["evals"], c["hops"]), c["name"]
 
 
-@pytest.mark.parametrize("L,W", [(64, 1), (16, 1), (128, 1), (64, 2), (512, 2), (10, 1)])
+@pytest.mark.parametrize("L,W", [(64, 1), (16, 1), (128, 1), (64, 2), (512, 2), (10, 1),
+                                 (64, 3), (128, 4), (512, 4)])
 def test_c1_u8_bit_exact(c1, L, W):
     q = c1["queries"]
     k = min(10, L)
@@ -76,6 +77,38 @@ def test_c1_u8_bit_exact(c1, L, W):
     assert np.array_equal(ids, oi)
     assert np.array_equal(d, od.astype(np.int64).clip(max=2**31 - 1).astype(np.int32))
     assert np.array_equal(ev, oe) and np.array_equal(hp, oh)
+
+
+@pytest.mark.parametrize("R,W", [(100, 1), (64, 2), (128, 1)])
+def test_u8_wide_rows_bit_exact(c1, R, W):
+    # unpruned K-NN graphs with up to 128 neighbour slots per step: ragged
+    # last slot (R = 100), and steps whose survivors need the 128-key sort
+    base = c1["base"][:4000]
+    g, _ = oracle.knn(base, base.astype(np.float64), R, exclude=np.arange(len(base), dtype=np.int32))
+    med = oracle.medoid(base)
+    h = make_index(base, g, med)
+    try:
+        q = c1["queries"]
+        ids, d, ev, hp, st = search(h, q, 10, 96, W=W)
+    finally:
+        ann.ann_free_index(h)
+    oi, od, oe, oh = oracle.search(base, g, q.astype(np.float64), med, 96, 10, W=W)
+    assert st == ann.OK
+    assert np.array_equal(ids, oi)
+    assert np.array_equal(d, od.astype(np.int64).astype(np.int32))
+    assert np.array_equal(ev, oe) and np.array_equal(hp, oh)
+
+
+@pytest.mark.parametrize("team,stage_rows", [(1, 32), (2, 4), (4, 8), (16, 16), (32, 5)])
+def test_c1_team_sizes_bit_exact(c1, team, stage_rows):
+    # every distance team size and gather round size gives the same exact
+    # int32 distances, hence the same search
+    q = c1["queries"]
+    ids, d, ev, hp, st = search(c1["h"], q, 10, 128, W=2, team=team, stage_rows=stage_rows)
+    oi, od, oe, oh = _oracle(c1, q, 128, 10, W=2)
+    assert st == ann.OK
+    assert np.array_equal(ids, oi) and np.array_equal(ev, oe) and np.array_equal(hp, oh)
+    assert np.array_equal(d, od.astype(np.int64).astype(np.int32))
 
 
 def test_c1_spill_to_global_table_stays_exact(c1):
@@ -129,6 +162,11 @@ def test_empty_batch_and_bad_device_inputs(c1):
     assert st == ann.ERR_INVALID_ARG
     assert (ids[1] == -1).all() and (ids[0] >= 0).all()
     assert ann.ann_sync_status(c1["h"]) == ann.OK  # cleared by the read
+    # host-side parameter checks return before any launch
+    for kw in (dict(team=3), dict(team=64), dict(stage_rows=33), dict(W=5), dict(hash_bits=7)):
+        with pytest.raises(ann.AnnError) as e:
+            search(c1["h"], q[:4], 10, 64, **kw)
+        assert e.value.status == ann.ERR_INVALID_ARG, kw
 
 
 @pytest.fixture(scope="module")
@@ -153,10 +191,10 @@ def _f32_parity(ids, d, oi, od, truth, scale=None):
     assert abs(r_gpu - r_or) <= 1e-3
 
 
-@pytest.mark.parametrize("L,W", [(32, 1), (64, 1), (128, 2)])
-def test_f32_l2_parity(f32_case, L, W):
+@pytest.mark.parametrize("L,W,team", [(32, 1, 0), (64, 1, 0), (128, 2, 0), (128, 2, 2), (128, 4, 32)])
+def test_f32_l2_parity(f32_case, L, W, team):
     q = f32_case["queries"]
-    ids, d, ev, hp, st = search(f32_case["h"], q, 10, L, W=W)
+    ids, d, ev, hp, st = search(f32_case["h"], q, 10, L, W=W, team=team)
     oi, od, oe, oh = _oracle(f32_case, q, L, 10, W=W)
     truth, _ = oracle.knn(f32_case["base"], q.astype(np.float64), 10)
     assert st == ann.OK
