@@ -23,8 +23,9 @@ Other workloads (`--workload`):
   ip       1M x 200 unit vectors, maximum inner product, out-of-distribution
            queries, 4,096 hubs; learned vs medoid at recall 0.90 / 0.95 / 0.99
   highdim  1M x 960 fp32, R = 48, 1,000 shifted queries, medoid entry; fp32
-           storage vs fp16 storage with the exact fp32 rerank, k = 10 and 100,
-           distance error against float64 recomputation
+           storage vs fp16 and int8-with-scale storage, each with and without
+           the exact fp32 rerank, k = 10 and 100, distance error against
+           float64 recomputation
   small    10,000 x 128 uint8 (the parity config), medoid entry, L = 64
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
@@ -51,7 +52,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "QPS at recall@10=0.95 on 1 GB300, learned vs medoid entry; dist evals/query"
-L_SWEEP = [16, 24, 32, 48, 64, 96, 128, 160, 192, 256, 320, 384, 512]
+L_SWEEP = [16, 24, 32, 40, 48, 56, 64, 72, 80, 88, 96, 112, 128, 144, 160, 176, 192, 224, 256, 320,
+           384, 448, 512]
 K_NN = 10
 
 WORKLOADS = {
@@ -63,16 +65,18 @@ WORKLOADS = {
         gen="shift_f32", n=1_000_000, nq=10_000, n_train=100_000, dim=128, R=32, metric="l2",
         dtype="f32", hubs=1024, learned=True, targets=[0.95]),
     "ip": dict(
-        desc=("ip_f32: N=1,000,000 unit fp32 d=200 (2,000-component normalised mixture), 10,000 "
-              "queries from a rotated, noisier mixture, maximum inner product, graph exact 64-NN + RNG "
+        desc=("ip_f32: N=1,000,000 unit fp32 d=200 (2,000-component normalised mixture, variance "
+              "spectrum (1+i)^-1), 10,000 queries from a different mixture (30% of the centres "
+              "Haar-rotated, twice the noise variance), maximum inner product, graph exact 64-NN + RNG "
               "prune R=32, k=10, 4,096 k-means hubs, BF16 query tower 200-256-64 trained on 100,000 "
               "labelled queries"),
         gen="ip_f32", n=1_000_000, nq=10_000, n_train=100_000, dim=200, R=32, metric="ip",
         dtype="f32", hubs=4096, learned=True, targets=[0.90, 0.95, 0.99]),
     "highdim": dict(
-        desc=("highdim_f32: N=1,000,000 fp32 d=960 (500-component low-rank mixture, 3.84 GB), 1,000 "
-              "mean-shifted queries, graph exact 64-NN + RNG prune R=48, medoid entry, fp32 storage vs "
-              "fp16 storage with exact fp32 rerank"),
+        desc=("highdim_f32: N=1,000,000 fp32 d=960 (500-component rank-64 mixture plus isotropic "
+              "noise, variance spectrum (1+i)^-1, 3.84 GB), 1,000 mean-shifted queries, graph exact "
+              "64-NN + RNG prune R=48, medoid entry, fp32 storage vs fp16 and int8-with-scale storage "
+              "with and without the exact fp32 rerank"),
         gen="highdim_f32", n=1_000_000, nq=1_000, n_train=0, dim=960, R=48, metric="l2",
         dtype="f32", hubs=0, learned=False, targets=[0.95], precision=True),
     "small": dict(
@@ -82,9 +86,10 @@ WORKLOADS = {
         hubs=0, learned=False, targets=[0.0], fixed_L=64),
     "batch": dict(
         desc=("batch_f32 (scaled from 10M to 2M base rows so that the exact-kNN graph builds in "
-              "seconds): N=2,000,000 fp32 d=96 (10,000-component mixture), 100,000 queries, half "
-              "shifted, per-query k in {1,10,100} and L uniform in [max(32,k),512], one persistent "
-              "launch; per-batch latency over batches of 1,000"),
+              "seconds): N=2,000,000 fp32 d=96 (10,000-component anisotropic mixture, variance "
+              "spectrum (1+i)^-1), 100,000 queries, half shifted, per-query k in {1,10,100} and L "
+              "uniform in [max(32,k),512], one persistent launch; per-batch latency over batches of "
+              "1,000"),
         gen="batch_f32", n=2_000_000, nq=100_000, n_train=0, dim=96, R=32, metric="l2",
         dtype="f32", hubs=0, learned=False, targets=[0.95], batching=True),
 }
@@ -376,8 +381,9 @@ def sweep(run, torch, ann, W, targets):
         if L < run.k:
             continue
         run.step(L, stats=True)
-        if ann.ann_sync_status(run.h, run.stream) != ann.OK:
-            raise RuntimeError("search reported a device error")
+        st = ann.ann_sync_status(run.h, run.stream)
+        if st != ann.OK:
+            raise RuntimeError(f"search at L={L} reported: {ann.status_string(st)}")
         r = recall(run.ids.cpu().numpy(), W["gt"], run.k)
         s = run.stats.cpu().numpy()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -508,17 +514,26 @@ def measure_mode(run, torch, ann, W, args, targets):
 
 
 def precision_report(W, torch, ann, args, dev):
-    """fp16 storage + exact fp32 rerank against fp32 storage (k = 10 and 100),
-    with the distance error of each against float64 recomputation."""
+    """fp16 storage and int8 storage with a per-row scale, each with and
+    without the exact fp32 rerank, against fp32 storage (k = 10 and 100), with
+    the distance error of each against float64 recomputation from the fp32
+    rows."""
     base = W["w"]["base"]
+    n, dim = base.shape
     h16 = ann.ann_index_create(base.astype(np.float16), W["graph"], W["medoid"], ann.F16, W["metric"],
                                device=dev.index or 0, base_f32=base)
+    packed = torch.empty((n, ann.ann_i8s_row_bytes(dim)), dtype=torch.uint8, device=dev)
+    ann.ann_quantize_i8s(W["base"], n, dim, packed)
+    h8 = ann.ann_index_create(packed, W["graph"], W["medoid"], ann.I8S, W["metric"], device=dev.index or 0,
+                              base_f32=base, n=n, dim=dim, degree=W["R"])
+    del packed
     out = {}
     q = W["w"]["queries"].astype(np.float64)
     try:
         for k in (10, 100):
             for name, h, flags in (("fp32", W["h"], 0), ("fp16_rerank", h16, ann.SEARCH_RERANK),
-                                   ("fp16", h16, 0)):
+                                   ("fp16", h16, 0), ("int8_rerank", h8, ann.SEARCH_RERANK),
+                                   ("int8", h8, 0)):
                 run = Runner(W, torch, ann, args, "medoid", h=h, flags=flags, k=k)
                 Lstar, sw, per = sweep(run, torch, ann, W, [0.95])
                 tm, sm, _ = timed(run, torch, ann, argparse.Namespace(warmup=2, steps=20), Lstar, 1, dev)
@@ -540,6 +555,7 @@ def precision_report(W, torch, ann, args, dev):
                                            mean_rel_dist_err_vs_fp64=float(rel.mean()))
     finally:
         ann.ann_free_index(h16)
+        ann.ann_free_index(h8)
     return out
 
 

@@ -42,8 +42,15 @@ typedef enum {
     ANN_ERR_UNSUPPORTED = 8
 } ann_status;
 
-/* element type of the stored base vectors */
-typedef enum { ANN_U8 = 0, ANN_F32 = 1, ANN_F16 = 2, ANN_BF16 = 3 } ann_dtype;
+/*
+ * Element type of the stored base vectors.  ANN_I8S is int8 with one scale
+ * per row (the precision line's int8 storage): a packed row is a 16-byte
+ * header (fp32 scale, then 12 zero bytes), the dim int8 codes, and zero bytes
+ * up to a multiple of 16 (ann_i8s_row_bytes); the row stands for
+ * x_j = scale * code_j.  Queries against every float type, ANN_I8S included,
+ * are fp32 rows.
+ */
+typedef enum { ANN_U8 = 0, ANN_F32 = 1, ANN_F16 = 2, ANN_BF16 = 3, ANN_I8S = 4 } ann_dtype;
 
 /* ANN_L2: squared Euclidean distance; ANN_IP: -<q, x> (maximum inner product) */
 typedef enum { ANN_L2 = 0, ANN_IP = 1 } ann_metric;
@@ -62,17 +69,20 @@ typedef struct ann_index ann_index;
  * Index description for ann_index_create.  The path searches a fixed-degree
  * proximity graph (Sec. 2.1, Def. 1) over base vectors D.
  *   n, dim       number of base vectors and their dimension; dim * element
- *                size must be a multiple of 16 bytes (16-byte row gathers)
+ *                size must be a multiple of 16 bytes (16-byte row gathers);
+ *                for ANN_I8S, dim must be a multiple of 4
  *   degree       R, slots per adjacency row, 1..ANN_MAX_STEP_CAND (a search
  *                expanding W entries per step needs W * R <= ANN_MAX_STEP_CAND)
  *   dtype,metric see ann_dtype / ann_metric; uint8 supports ANN_L2 only
- *   base         n*dim elements of dtype, row-major (host or device pointer)
+ *   base         n*dim elements of dtype, row-major (host or device pointer);
+ *                for ANN_I8S, n packed rows made by ann_quantize_i8s
  *   graph        n*degree int32 node ids, row-major; -1 marks an unused
  *                slot (host or device pointer)
  *   medoid       entry node used when no per-query entry is given (the
  *                navigating node of Sec. 2.1)
  *   base_f32     optional n*dim fp32 rows (host or device) kept for the exact
- *                rerank of reduced-precision (F16/BF16) storage; may be NULL
+ *                rerank of reduced-precision (F16/BF16/I8S) storage; may be
+ *                NULL
  * The index copies everything it is given; the caller keeps ownership.
  */
 typedef struct {
@@ -140,6 +150,19 @@ const char *ann_status_string(ann_status s);
  * on success.
  */
 ann_status ann_index_create(const ann_index_desc *desc, int device, ann_index **out);
+
+/* Bytes of one packed ANN_I8S row of dim codes: 16 + dim rounded up to 16. */
+int32_t ann_i8s_row_bytes(int32_t dim);
+
+/*
+ * Quantise n fp32 rows of dim values (device pointer d_x, row-major) into n
+ * packed ANN_I8S rows at d_rows (device, n * ann_i8s_row_bytes(dim) bytes,
+ * 16-byte aligned; caller-owned).  Per row, in fp32: scale = max_j |x_j| /
+ * 127; code_j = x_j / scale rounded half to even and clipped to [-127, 127];
+ * an all-zero row gets scale 0 and zero codes.  dim must be a multiple of 4.
+ * Asynchronous on stream.
+ */
+ann_status ann_quantize_i8s(const float *d_x, int64_t n, int32_t dim, void *d_rows, void *stream);
 
 /* Free an index and its device memory (NULL is accepted).  Synchronises the device. */
 ann_status ann_free_index(ann_index *idx);

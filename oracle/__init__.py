@@ -22,7 +22,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _LIB = None
 
-U8, F32 = 0, 1
+U8, F32, F64 = 0, 1, 2
 L2, IP = 0, 1
 INT32_MAX = 2**31 - 1
 
@@ -82,7 +82,9 @@ def _base(x):
         return x, U8
     if x.dtype == np.float32:
         return x, F32
-    raise TypeError("base rows must be uint8 or float32")
+    if x.dtype == np.float64:
+        return x, F64
+    raise TypeError("base rows must be uint8, float32 or float64")
 
 
 def num_threads() -> int:
@@ -316,3 +318,23 @@ def rerank(base_exact, pool_ids, queries, k, metric=L2):
         ids[i, :len(order)] = [p[j] for j in order]
         dists[i, :len(order)] = [d[j] for j in order]
     return ids, dists
+
+
+def quantize_i8s(x):
+    """int8 codes with one scale per row, as the precision line's int8
+    storage reads: in fp32, scale = max_j |x_j| / 127 and code_j = x_j / scale
+    rounded half to even, clipped to [-127, 127]; an all-zero row gets scale 0
+    and zero codes.  Returns (codes int8 [n, d], scales float32 [n])."""
+    x = np.ascontiguousarray(x, np.float32)
+    scale = (np.abs(x).max(axis=1) / np.float32(127)).astype(np.float32)
+    safe = np.where(scale > 0, scale, np.float32(1)).astype(np.float32)
+    q = np.rint(x / safe[:, None])
+    q = np.clip(q, -127, 127)
+    q[scale == 0] = 0
+    return q.astype(np.int8), scale
+
+
+def dequantize_i8s(codes, scales):
+    """The rows int8 storage stands for, x_j = scale * code_j, exact in
+    float64 (a 24-bit by 8-bit product)."""
+    return np.asarray(codes, np.float64) * np.asarray(scales, np.float64)[:, None]

@@ -7,6 +7,9 @@
  * the benchmark.  The product library never links, loads or calls it, and it
  * shares no code, header or table with the CUDA path.
  *
+ * Row types: uint8, float32 and float64 (the last for rows dequantized from
+ * int8 codes with a per-row scale: code * scale is exact in double).
+ *
  * Arithmetic: every floating-point distance is accumulated in double
  * precision; uint8 data give integer squared distances that double holds
  * exactly (128 * 255^2 < 2^53).  Every ordering is the lexicographic order on
@@ -41,6 +44,7 @@
 
 #define OR_U8 0
 #define OR_F32 1
+#define OR_F64 2
 #define OR_L2 0
 #define OR_IP 1
 
@@ -54,6 +58,8 @@ static double base_at(const void *base, int dtype, int64_t i, int d, int j)
 {
     if (dtype == OR_U8)
         return (double)((const uint8_t *)base)[i * (int64_t)d + j];
+    if (dtype == OR_F64)
+        return ((const double *)base)[i * (int64_t)d + j];
     return (double)((const float *)base)[i * (int64_t)d + j];
 }
 

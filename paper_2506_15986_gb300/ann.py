@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(PKG, "libann.so")
 # ann_status
 OK, ERR_INVALID_ARG, ERR_IO, ERR_FORMAT, ERR_OOM, ERR_CUDA, ERR_CAPACITY, ERR_TIMEOUT, ERR_UNSUPPORTED = range(9)
 # ann_dtype / ann_metric
-U8, F32, F16, BF16 = 0, 1, 2, 3
+U8, F32, F16, BF16, I8S = 0, 1, 2, 3, 4
 L2, IP = 0, 1
 SEARCH_RERANK = 1
 MAX_L, MAX_W, MAX_STEP_CAND = 512, 4, 128
@@ -72,6 +72,8 @@ def load_library(path: str | None = None):
     sig = {
         "ann_status_string": ([i32], _c.c_char_p),
         "ann_index_create": ([_c.POINTER(ann_index_desc), i32, pp], i32),
+        "ann_i8s_row_bytes": ([i32], i32),
+        "ann_quantize_i8s": ([_p, i64, i32, _p, _p], i32),
         "ann_free_index": ([_p], i32),
         "ann_index_info": ([_p] + [_p] * 8, i32),
         "ann_save_index": ([_p, _c.c_char_p], i32),
@@ -155,6 +157,16 @@ def ann_index_create(base, graph, medoid, dtype, metric=L2, device=0, base_f32=N
     _check(load_library().ann_index_create(ctypes.byref(d), int(device), ctypes.byref(h)),
            "ann_index_create")
     return h.value
+
+
+def ann_i8s_row_bytes(dim):
+    return int(load_library().ann_i8s_row_bytes(int(dim)))
+
+
+def ann_quantize_i8s(x, n, dim, rows, stream=None):
+    """Quantise n fp32 rows (device) into packed int8-with-scale rows (device)."""
+    _check(load_library().ann_quantize_i8s(_ptr(x), int(n), int(dim), _ptr(rows), _stream(stream)),
+           "ann_quantize_i8s")
 
 
 def ann_free_index(h):

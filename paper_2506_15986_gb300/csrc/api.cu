@@ -21,8 +21,18 @@ int elem_size(int dtype)
     case ANN_F32: return 4;
     case ANN_F16: return 2;
     case ANN_BF16: return 2;
+    case ANN_I8S: return 1;
     default: return 0;
     }
+}
+
+int64_t row_bytes(int dtype, int dim)
+{
+    if (dim < 1)
+        return 0;
+    if (dtype == ANN_I8S)
+        return 16 + (static_cast<int64_t>(dim) + 15) / 16 * 16;
+    return static_cast<int64_t>(dim) * elem_size(dtype);
 }
 
 ann_status cuda_status(cudaError_t e)
@@ -143,15 +153,14 @@ ann_status ann_index_create(const ann_index_desc *desc, int device, ann_index **
 {
     if (!desc || !out)
         return ANN_ERR_INVALID_ARG;
-    const int es = elem_size(desc->dtype);
+    const int64_t rowbytes = row_bytes(desc->dtype, desc->dim);
     if (desc->n < 1 || desc->n > INT32_MAX || desc->dim < 1 || desc->degree < 1 ||
-        desc->degree > ANN_MAX_STEP_CAND || es == 0 || (desc->metric != ANN_L2 && desc->metric != ANN_IP) ||
+        desc->degree > ANN_MAX_STEP_CAND || rowbytes == 0 || (desc->metric != ANN_L2 && desc->metric != ANN_IP) ||
         !desc->base || !desc->graph || desc->medoid < 0 || desc->medoid >= desc->n)
         return ANN_ERR_INVALID_ARG;
     if (desc->dtype == ANN_U8 && desc->metric != ANN_L2)
         return ANN_ERR_UNSUPPORTED;
-    const int64_t rowbytes = static_cast<int64_t>(desc->dim) * es;
-    if (rowbytes % 16 != 0 || rowbytes > 16384)
+    if (rowbytes % 16 != 0 || rowbytes > 16384 || (desc->dtype == ANN_I8S && desc->dim % 4 != 0))
         return ANN_ERR_INVALID_ARG;
     if (desc->base_f32 && desc->dtype == ANN_U8)
         return ANN_ERR_INVALID_ARG;
@@ -321,10 +330,10 @@ ann_status ann_load_index(const char *path, int device, ann_index **out)
         fclose(f);
         return ANN_ERR_FORMAT;
     }
-    const int es = elem_size(h.dtype);
+    const int64_t rb = row_bytes(h.dtype, h.dim);
     bool sane = memcmp(h.magic, kMagic, 8) == 0 && h.version == kVersion &&
                 h.header_bytes == sizeof(FileHeader) && h.n >= 1 && h.n <= INT32_MAX && h.dim >= 1 &&
-                h.degree >= 1 && es > 0 && h.bytes_base == static_cast<uint64_t>(h.n) * h.dim * es &&
+                h.degree >= 1 && rb > 0 && h.bytes_base == static_cast<uint64_t>(h.n) * rb &&
                 h.bytes_graph == static_cast<uint64_t>(h.n) * h.degree * 4 &&
                 h.bytes_f32 == ((h.flags & 1u) ? static_cast<uint64_t>(h.n) * h.dim * 4 : 0);
     if (!sane) {

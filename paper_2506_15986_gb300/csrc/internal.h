@@ -35,6 +35,8 @@ constexpr int kStatusTimeoutBit = 2;
 constexpr int kStatusBadInputBit = 4;
 
 int elem_size(int dtype);
+// bytes of one stored base row (0 for an unknown dtype or dim < 1)
+int64_t row_bytes(int dtype, int dim);
 
 // status helpers
 ann_status cuda_status(cudaError_t e);

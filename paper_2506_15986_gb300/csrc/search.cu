@@ -14,8 +14,9 @@
 //   - the visited set: an open-addressing hash table (linear probing, key
 //     id+1, 0 = empty).  When it would pass 3/4 load, its entries move to a
 //     per-team table in global scratch that takes every later insert, so
-//     the set stays exact; when that one would pass 3/4 load the query fails
-//     with a capacity status.
+//     the set stays exact; that one hands over in turn to a four times
+//     larger global table, and only when the last would pass 3/4 load does
+//     the query fail with a capacity status.
 // Semantics follow the sorted-pool reading of Algorithm 1: single entry, a
 // node is visited when its distance is computed, a step expands the first W
 // unexpanded pool entries, the pool is truncated to L, the search stops when
@@ -45,6 +46,7 @@ struct SearchArgs {
     int dim, R, rowbytes;
     const uint8_t *queries;
     int qbytes;
+    int qpad;  // zero bytes after the query row in shared memory
     int64_t nq;
     int64_t qdiv;  // work item i reads query row and target i / qdiv
     const int32_t *entries;
@@ -106,14 +108,17 @@ __device__ __forceinline__ int visit(uint32_t *htab, int hbits, bool global_mode
 
 // Visited test-and-insert for NS ids per lane (-1 = none) in one table.
 // res[s] = 1 when ids[s] was not yet visited (and is now), 0 when it was, -1
-// when the table is full.  All first probes go out before the collision
-// chains are followed, so their latencies overlap.  Concurrent inserts of the
-// same id (from any lane or slot) give exactly one 1.
+// when the table is full.  All first probes go out before any result is
+// used, and the collision chains of all slots advance together, so their
+// latencies overlap.  Concurrent inserts of the same id (from any lane or
+// slot) give exactly one 1: every insert of a key walks the same probe
+// sequence and the compare-and-swap decides each slot once.
 template <int NS>
 __device__ __forceinline__ void visit_slots(uint32_t *tab, int bits, const int32_t (&ids)[NS], int (&res)[NS])
 {
     const uint32_t mask = (1u << bits) - 1u;
     uint32_t h[NS];
+    bool more = false;
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
         res[s] = 0;
@@ -123,24 +128,50 @@ __device__ __forceinline__ void visit_slots(uint32_t *tab, int bits, const int32
             h[s] = hash_slot(key, bits);
             const uint32_t old = atomicCAS(&tab[h[s]], 0u, key);
             res[s] = old == 0u ? 1 : (old == key ? 0 : 2);
+            more |= res[s] == 2;
         }
     }
+    for (uint32_t p = 1; p <= mask && more; ++p) {
+        more = false;
 #pragma unroll
-    for (int s = 0; s < NS; ++s) {
-        if (res[s] == 2) {
-            const uint32_t key = static_cast<uint32_t>(ids[s]) + 1u;
-            uint32_t g = h[s];
-            res[s] = -1;
-            for (uint32_t p = 1; p <= mask; ++p) {
-                g = (g + 1u) & mask;
-                const uint32_t old = atomicCAS(&tab[g], 0u, key);
-                if (old == 0u || old == key) {
-                    res[s] = old == 0u ? 1 : 0;
-                    break;
-                }
+        for (int s = 0; s < NS; ++s) {
+            if (res[s] == 2) {
+                const uint32_t key = static_cast<uint32_t>(ids[s]) + 1u;
+                h[s] = (h[s] + 1u) & mask;
+                const uint32_t old = atomicCAS(&tab[h[s]], 0u, key);
+                res[s] = old == 0u ? 1 : (old == key ? 0 : 2);
+                more |= res[s] == 2;
             }
         }
     }
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+        if (res[s] == 2)
+            res[s] = -1;  // every slot probed: the table is full
+}
+
+// Moves every key of the table src (2^sbits slots; in global memory when
+// src_global) into the global table dst (2^dbits slots), which is cleared
+// first.  The whole warp calls it.
+__device__ __forceinline__ void migrate_keys(const uint32_t *src, int sbits, bool src_global, uint32_t *dst,
+                                             int dbits, int lane)
+{
+    for (int o = lane; o < (1 << dbits) / 4; o += 32)
+        reinterpret_cast<uint4 *>(dst)[o] = make_uint4(0u, 0u, 0u, 0u);
+    __syncwarp();
+    const uint32_t dmask = (1u << dbits) - 1u;
+    for (int o = lane; o < (1 << sbits); o += 32) {
+        const uint32_t key = src_global ? __ldcg(src + o) : src[o];
+        if (key == 0u)
+            continue;
+        uint32_t g = hash_slot(key, dbits);
+        for (uint32_t pr = 0; pr <= dmask; ++pr) {
+            if (atomicCAS(&dst[g], 0u, key) == 0u)
+                break;
+            g = (g + 1u) & dmask;
+        }
+    }
+    __syncwarp();
 }
 
 // Distance of one staged row to the query, computed by a team of G lanes
@@ -172,22 +203,68 @@ __device__ __forceinline__ uint32_t group_distance(const uint8_t *row, const uin
         for (int o = G >> 1; o > 0; o >>= 1)
             acc += __shfl_xor_sync(kFull, acc, o);
         return acc;  // exact non-negative int32, ordered as unsigned
-    } else {
+    } else if constexpr (DT == ANN_I8S) {
+        // x_j = scale * code_j.  L2: sum of (q_j - scale * code_j)^2, each
+        // difference from one fused multiply-add; IP: scale * sum q_j code_j.
+        // The query buffer is zero beyond dim, where the codes are zero too.
+        const float scale = *reinterpret_cast<const float *>(row);
+        const uint4 *c4 = reinterpret_cast<const uint4 *>(row + 16);
         const float4 *q4 = reinterpret_cast<const float4 *>(q);
         float a0 = 0.f, a1 = 0.f;
-        auto acc4 = [&](float x0, float x1, float x2, float x3, float4 y) {
-            if constexpr (MT == ANN_L2) {
-                const float d0 = x0 - y.x, d1 = x1 - y.y, d2 = x2 - y.z, d3 = x3 - y.w;
-                a0 = fmaf(d0, d0, a0);
-                a1 = fmaf(d1, d1, a1);
-                a0 = fmaf(d2, d2, a0);
-                a1 = fmaf(d3, d3, a1);
-            } else {
-                a0 = fmaf(x0, y.x, a0);
-                a1 = fmaf(x1, y.y, a1);
-                a0 = fmaf(x2, y.z, a0);
-                a1 = fmaf(x3, y.w, a1);
+        for (int c = sub; c < chunks - 1; c += G) {
+            const uint4 x = c4[c];
+            const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float4 y = q4[4 * c + k];
+                const float c0 = static_cast<float>(static_cast<int8_t>(w[k] & 0xffu));
+                const float c1 = static_cast<float>(static_cast<int8_t>((w[k] >> 8) & 0xffu));
+                const float c2 = static_cast<float>(static_cast<int8_t>((w[k] >> 16) & 0xffu));
+                const float c3 = static_cast<float>(static_cast<int8_t>(w[k] >> 24));
+                if constexpr (MT == ANN_L2) {
+                    const float d0 = fmaf(-scale, c0, y.x), d1 = fmaf(-scale, c1, y.y);
+                    const float d2 = fmaf(-scale, c2, y.z), d3 = fmaf(-scale, c3, y.w);
+                    a0 = fmaf(d0, d0, a0);
+                    a1 = fmaf(d1, d1, a1);
+                    a0 = fmaf(d2, d2, a0);
+                    a1 = fmaf(d3, d3, a1);
+                } else {
+                    a0 = fmaf(c0, y.x, a0);
+                    a1 = fmaf(c1, y.y, a1);
+                    a0 = fmaf(c2, y.z, a0);
+                    a1 = fmaf(c3, y.w, a1);
+                }
             }
+        }
+        float s = a0 + a1;
+        for (int o = G >> 1; o > 0; o >>= 1)
+            s += __shfl_xor_sync(kFull, s, o);
+        if constexpr (MT == ANN_IP)
+            s = -(scale * s);
+        return f32_to_ord(s);
+    } else {
+        const float4 *q4 = reinterpret_cast<const float4 *>(q);
+        // two FP32 accumulators (even and odd coordinates) held as one packed
+        // pair: each f32x2 operation rounds both halves exactly as the scalar
+        // operations would, at half the instruction count
+        uint64_t acc = 0;  // (0.f, 0.f)
+        auto acc4 = [&](float x0, float x1, float x2, float x3, float4 y) {
+            if constexpr (MT == ANN_L2)
+                asm("{\n\t.reg .b64 x, y, d;\n\t"
+                    "mov.b64 x, {%1, %2};\n\tmov.b64 y, {%5, %6};\n\t"
+                    "sub.rn.f32x2 d, x, y;\n\tfma.rn.f32x2 %0, d, d, %0;\n\t"
+                    "mov.b64 x, {%3, %4};\n\tmov.b64 y, {%7, %8};\n\t"
+                    "sub.rn.f32x2 d, x, y;\n\tfma.rn.f32x2 %0, d, d, %0;\n\t}"
+                    : "+l"(acc)
+                    : "f"(x0), "f"(x1), "f"(x2), "f"(x3), "f"(y.x), "f"(y.y), "f"(y.z), "f"(y.w));
+            else
+                asm("{\n\t.reg .b64 x, y;\n\t"
+                    "mov.b64 x, {%1, %2};\n\tmov.b64 y, {%5, %6};\n\t"
+                    "fma.rn.f32x2 %0, x, y, %0;\n\t"
+                    "mov.b64 x, {%3, %4};\n\tmov.b64 y, {%7, %8};\n\t"
+                    "fma.rn.f32x2 %0, x, y, %0;\n\t}"
+                    : "+l"(acc)
+                    : "f"(x0), "f"(x1), "f"(x2), "f"(x3), "f"(y.x), "f"(y.y), "f"(y.z), "f"(y.w));
         };
         if constexpr (DT == ANN_F32) {
             const float4 *x4 = reinterpret_cast<const float4 *>(row);
@@ -215,7 +292,7 @@ __device__ __forceinline__ uint32_t group_distance(const uint8_t *row, const uin
                 acc4(f2.x, f2.y, f3.x, f3.y, q4[2 * c + 1]);
             }
         }
-        float s = a0 + a1;
+        float s = __uint_as_float(static_cast<uint32_t>(acc)) + __uint_as_float(static_cast<uint32_t>(acc >> 32));
         for (int o = G >> 1; o > 0; o >>= 1)
             s += __shfl_xor_sync(kFull, s, o);
         if constexpr (MT == ANN_IP)
@@ -241,7 +318,10 @@ __global__ void __launch_bounds__(32 * kSearchWarps) beam_search_kernel(const Se
     int32_t *cids = reinterpret_cast<int32_t *>(my + a.off_cids);
     uint32_t *htab = reinterpret_cast<uint32_t *>(my + a.off_hash);
     const int team = blockIdx.x * kSearchWarps + wid;
-    uint32_t *gtab = a.spill + (static_cast<size_t>(team) << a.spill_bits);
+    // two global spill tables per team: 2^spill_bits slots, then one four
+    // times larger for the rare query that outgrows the first
+    uint32_t *gtab1 = a.spill + static_cast<size_t>(team) * (static_cast<size_t>(5) << a.spill_bits);
+    uint32_t *gtab2 = gtab1 + (static_cast<size_t>(1) << a.spill_bits);
 
     if (lane == 0) {
         mbar_init(bar, 1);
@@ -251,7 +331,6 @@ __global__ void __launch_bounds__(32 * kSearchWarps) beam_search_kernel(const Se
     uint32_t phase = 0;
     const int hcap = 1 << a.hash_bits;
     const int hlimit = hcap * 3 / 4;
-    const int glimit = (1 << a.spill_bits) * 3 / 4;
 
     for (;;) {
         long long qi = 0;
@@ -274,27 +353,33 @@ __global__ void __launch_bounds__(32 * kSearchWarps) beam_search_kernel(const Se
                 atomicOr(a.status, kStatusBadInputBit);
         }
 
-        int cnt = 0, cursor = 0, evals = 0, hops = 0, hused = 0, gused = 0;
+        int cnt = 0, cursor = 0, evals = 0, hops = 0;
+        // visited set: level 0 = the shared table, 1 and 2 = the global ones;
+        // used = keys in the current table, limit = its 3/4 load
+        int level = 0, used = 0, limit = hlimit, gbits = a.spill_bits;
+        uint32_t *gtab = gtab1;
         int32_t *pred = sel + ANN_MAX_W;  // predicted ids of the next selection
         int npred = 0;
         int32_t nxt[kSlots];  // their adjacency rows, lane-distributed like cur[]
 #pragma unroll
         for (int r = 0; r < kSlots; ++r)
             nxt[r] = -1;
-        bool gmode = false, found = false;
+        bool found = false;
         if (!failed) {
             // query row -> shared memory; clear the visited table
             const uint8_t *qsrc = a.queries + qrow * a.qbytes;
             for (int o = lane * 16; o < a.qbytes; o += 32 * 16)
                 *reinterpret_cast<uint4 *>(qbuf + o) = *reinterpret_cast<const uint4 *>(qsrc + o);
+            for (int o = a.qbytes + lane * 4; o < a.qbytes + a.qpad; o += 32 * 4)
+                *reinterpret_cast<float *>(qbuf + o) = 0.f;
             for (int o = lane; o < hcap / 4; o += 32)
                 reinterpret_cast<uint4 *>(htab)[o] = make_uint4(0u, 0u, 0u, 0u);
             __syncwarp();
             if (lane == 0) {
-                visit(htab, a.hash_bits, false, gtab, a.spill_bits, entry);
+                visit(htab, a.hash_bits, false, gtab1, a.spill_bits, entry);
                 cids[0] = entry;
             }
-            hused = 1;
+            used = 1;
             evals = 1;
             found = (entry == target);
         }
@@ -489,30 +574,23 @@ __global__ void __launch_bounds__(32 * kSearchWarps) beam_search_kernel(const Se
             }
 
             // ---- neighbours of the selected entries: visited test, compaction
-            if (!gmode && hused + total > hlimit) {
-                // continue in the global table: clear it, then move the shared
-                // table's entries into it so that every later lookup probes
-                // one table only
-                gmode = true;
-                for (int o = lane; o < (1 << a.spill_bits) / 4; o += 32)
-                    reinterpret_cast<uint4 *>(gtab)[o] = make_uint4(0u, 0u, 0u, 0u);
-                __syncwarp();
-                const uint32_t gmask = (1u << a.spill_bits) - 1u;
-                for (int o = lane; o < hcap; o += 32) {
-                    const uint32_t key = htab[o];
-                    if (key == 0u)
-                        continue;
-                    uint32_t g = hash_slot(key, a.spill_bits);
-                    for (uint32_t pr = 0; pr <= gmask; ++pr) {
-                        if (atomicCAS(&gtab[g], 0u, key) == 0u)
-                            break;
-                        g = (g + 1u) & gmask;
-                    }
-                }
-                gused = hused;
-                __syncwarp();
+            // A table that would pass 3/4 load hands its keys to the next,
+            // larger one (shared -> global -> 4x larger global), which takes
+            // every later insert, so a lookup probes one table only and the
+            // set stays exact.
+            while (used + total > limit && level < 2) {
+                uint32_t *dst = level == 0 ? gtab1 : gtab2;
+                const int dbits = level == 0 ? a.spill_bits : a.spill_bits + 2;
+                if (level == 0)
+                    migrate_keys(htab, a.hash_bits, false, dst, dbits, lane);
+                else
+                    migrate_keys(gtab, gbits, true, dst, dbits, lane);
+                gtab = dst;
+                gbits = dbits;
+                limit = (1 << dbits) * 3 / 4;
+                ++level;
             }
-            if (gmode && gused + total > glimit) {
+            if (used + total > limit) {
                 failed = true;
                 if (lane == 0)
                     atomicOr(a.status, kStatusCapacityBit);
@@ -527,8 +605,8 @@ __global__ void __launch_bounds__(32 * kSearchWarps) beam_search_kernel(const Se
                 const int32_t id = lane + 32 * s < total ? cur[s] : -1;
                 vid[s] = (id >= 0 && id < a.n) ? id : -1;
             }
-            if (gmode)
-                visit_slots<kSlots>(gtab, a.spill_bits, vid, res);
+            if (level > 0)
+                visit_slots<kSlots>(gtab, gbits, vid, res);
             else
                 visit_slots<kSlots>(htab, a.hash_bits, vid, res);
             nc = 0;
@@ -554,10 +632,7 @@ __global__ void __launch_bounds__(32 * kSearchWarps) beam_search_kernel(const Se
                 break;
             }
             evals += nc;
-            if (gmode)
-                gused += nc;
-            else
-                hused += nc;
+            used += nc;
             __syncwarp();
         }
 
@@ -701,6 +776,8 @@ ann_status launch_typed(const SearchArgs &a, size_t smem, int teams, cudaStream_
     case ANN_F16 * 2 + ANN_IP: st = FN<ANN_F16, ANN_IP>(__VA_ARGS__); break;         \
     case ANN_BF16 * 2 + ANN_L2: st = FN<ANN_BF16, ANN_L2>(__VA_ARGS__); break;       \
     case ANN_BF16 * 2 + ANN_IP: st = FN<ANN_BF16, ANN_IP>(__VA_ARGS__); break;       \
+    case ANN_I8S * 2 + ANN_L2: st = FN<ANN_I8S, ANN_L2>(__VA_ARGS__); break;         \
+    case ANN_I8S * 2 + ANN_IP: st = FN<ANN_I8S, ANN_IP>(__VA_ARGS__); break;         \
     default: st = ANN_ERR_UNSUPPORTED; break;                                        \
     }
 
@@ -717,7 +794,7 @@ int default_team(int rowbytes)
 
 size_t search_scratch_bytes(int teams, int spill_bits)
 {
-    return 256 + static_cast<size_t>(teams) * (static_cast<size_t>(4) << spill_bits);
+    return 256 + static_cast<size_t>(teams) * (static_cast<size_t>(20) << spill_bits);
 }
 
 ann_status launch_search(ann_index *idx, const SearchLaunch &L, cudaStream_t s)
@@ -732,6 +809,9 @@ ann_status launch_search(ann_index *idx, const SearchLaunch &L, cudaStream_t s)
     a.rowbytes = idx->rowbytes;
     a.queries = static_cast<const uint8_t *>(L.queries);
     a.qbytes = L.qbytes;
+    // int8 rows are read in whole 16-code chunks: the query is zero-extended
+    // to the padded code count
+    a.qpad = idx->dtype == ANN_I8S ? 4 * ((idx->dim + 15) / 16 * 16 - idx->dim) : 0;
     a.nq = L.nq;
     a.qdiv = L.qdiv > 0 ? L.qdiv : 1;
     a.entries = L.entries;
@@ -757,9 +837,10 @@ ann_status launch_search(ann_index *idx, const SearchLaunch &L, cudaStream_t s)
             ++hb;
     }
     a.hash_bits = hb;
-    // spill tables hold 40 evaluations per pool slot below 3/4 load (about 3x
-    // the typical count): small enough to stay mostly L2-resident and cheap
-    // to clear when a query starts spilling
+    // the first spill table holds 40 evaluations per pool slot below 3/4 load
+    // (about 3x the typical count), small enough to stay mostly L2-resident
+    // and cheap to clear when a query starts spilling; the second holds four
+    // times more for the tail
     int sb = 12;
     while ((1 << sb) * 3 / 4 < 40 * p->L && sb < 15)
         ++sb;
@@ -791,7 +872,7 @@ ann_status launch_search(ann_index *idx, const SearchLaunch &L, cudaStream_t s)
     a.off_sel = static_cast<int>(off);
     off = align_up(off + 4 * 2 * ANN_MAX_W, 16);  // selected and predicted ids
     a.off_q = static_cast<int>(off);
-    off = align_up(off + L.qbytes, 16);
+    off = align_up(off + L.qbytes + a.qpad, 16);
     a.off_stage = static_cast<int>(off);
     off = align_up(off + static_cast<size_t>(a.stage_rows) * a.stage_stride, 16);
     a.off_pool = static_cast<int>(off);
@@ -819,7 +900,7 @@ ann_status launch_search(ann_index *idx, const SearchLaunch &L, cudaStream_t s)
     if (teams < 1)
         return ANN_OK;
 
-    // scratch: work counter, then one spill table per team
+    // scratch: work counter, then two spill tables per team
     const size_t need = search_scratch_bytes(teams, a.spill_bits);
     void *scratch = L.scratch;
     const bool own = scratch == nullptr;

@@ -94,24 +94,34 @@ def shift_f32(n=1_000_000, nq=10_000, n_train=100_000, d=128, n_comp=1000,
     return dict(base=base, queries=q, train=train)
 
 
-def highdim_f32(n=1_000_000, nq=1_000, d=960, rank=64, n_comp=500,
-                seed=SEED_BASE + 3):
+def _spectrum(d, exponent):
+    """Global per-dimension scale (1 + i)^-exponent: descriptor-like data with
+    a low intrinsic dimension, on which proximity graphs stay navigable."""
+    return ((1.0 + np.arange(d)) ** (-exponent)).astype(np.float32)
+
+
+def highdim_f32(n=1_000_000, nq=1_000, d=960, rank=64, n_comp=500, centre_scale=0.5,
+                spectrum=0.5, noise=0.1, seed=SEED_BASE + 3):
+    """GIST-shaped rows: a mixture of rank-64 Gaussians plus isotropic noise,
+    all under the global spectrum; queries shifted by one global offset."""
     rng = _rng(seed)
-    centres = rng.normal(0.0, 4.0, size=(n_comp, d)).astype(np.float32)
+    g = _spectrum(d, spectrum)
+    centres = (rng.normal(0.0, centre_scale, size=(n_comp, d)) * g).astype(np.float32)
     A = (rng.standard_normal((n_comp, d, rank)) / np.sqrt(rank)).astype(np.float32)
+    A *= g[None, :, None]
     comp = rng.integers(0, n_comp, size=n)
     base = np.empty((n, d), np.float32)
-    for s, e in _chunks(n, 1 << 16):
+    for s, e in _chunks(n, 1 << 15):
         c = comp[s:e]
         zl = rng.standard_normal((e - s, rank), dtype=np.float32)
         eps = rng.standard_normal((e - s, d), dtype=np.float32)
         low = np.einsum("ndr,nr->nd", A[c], zl, optimize=True)
-        base[s:e] = centres[c] + low + 0.1 * eps
-    shift = rng.normal(0.0, 0.5, size=d).astype(np.float32)
+        base[s:e] = centres[c] + low + noise * g * eps
+    shift = (rng.normal(0.0, 0.5 * centre_scale, size=d) * g).astype(np.float32)
     qc = rng.integers(0, n_comp, size=nq)
     zl = rng.standard_normal((nq, rank), dtype=np.float32)
     eps = rng.standard_normal((nq, d), dtype=np.float32)
-    q = centres[qc] + np.einsum("ndr,nr->nd", A[qc], zl) + 0.1 * eps + shift
+    q = centres[qc] + np.einsum("ndr,nr->nd", A[qc], zl) + noise * g * eps + shift
     return dict(base=base, queries=q.astype(np.float32))
 
 
@@ -119,18 +129,22 @@ def _normalise(x):
     return (x / np.linalg.norm(x, axis=1, keepdims=True)).astype(np.float32)
 
 
-def ip_f32(n=1_000_000, nq=10_000, n_train=0, d=200, n_comp=2000, noise=0.05,
+def ip_f32(n=1_000_000, nq=10_000, n_train=0, d=200, n_comp=2000, noise=0.5, spectrum=0.5,
            rot_frac=0.3, seed=SEED_BASE + 4):
+    """Unit rows around normalised centres (von Mises-Fisher-like), all under
+    the global spectrum; queries from a different mixture: a Haar rotation of
+    30% of the centres and twice the noise variance."""
     rng = _rng(seed)
-    mu = _normalise(rng.standard_normal((n_comp, d)))
+    g = _spectrum(d, spectrum)
+    mu = _normalise(rng.standard_normal((n_comp, d)) * g)
     base = np.empty((n, d), np.float32)
     for s, e in _chunks(n):
         comp = rng.integers(0, n_comp, size=e - s)
         z = rng.standard_normal((e - s, d), dtype=np.float32)
-        base[s:e] = _normalise(mu[comp] + noise * z)
+        base[s:e] = _normalise(mu[comp] + noise * g * z)
     # Haar rotation: QR of a Gaussian matrix with the sign fix on R's diagonal
-    g = rng.standard_normal((d, d))
-    Qm, Rm = np.linalg.qr(g)
+    gm = rng.standard_normal((d, d))
+    Qm, Rm = np.linalg.qr(gm)
     Qm = Qm * np.sign(np.diag(Rm))[None, :]
     mu_q = mu.copy()
     rot = rng.permutation(n_comp)[: int(round(rot_frac * n_comp))]
@@ -139,25 +153,30 @@ def ip_f32(n=1_000_000, nq=10_000, n_train=0, d=200, n_comp=2000, noise=0.05,
     def queries(m):
         comp = rng.integers(0, n_comp, size=m)
         z = rng.standard_normal((m, d), dtype=np.float32)
-        return _normalise(mu_q[comp] + np.sqrt(2.0) * noise * z)
+        return _normalise(mu_q[comp] + np.sqrt(2.0) * noise * g * z)
 
     q = queries(nq)
     train = queries(n_train) if n_train else np.empty((0, d), np.float32)
     return dict(base=base, queries=q, train=train)
 
 
-def batch_f32(n=10_000_000, nq=100_000, d=96, n_comp=10_000,
+def batch_f32(n=10_000_000, nq=100_000, d=96, n_comp=10_000, centre_scale=1.0, spectrum=0.5,
               seed=SEED_BASE + 5):
+    """The shifted-mixture law of shift_f32 at d = 96 with 10,000 components;
+    half of the query stream shifted; per-query k in {1, 10, 100} and L
+    uniform in [max(32, k), 512]."""
     rng = _rng(seed)
-    centres = rng.normal(0.0, 4.0, size=(n_comp, d)).astype(np.float32)
-    shifts = (0.5 * rng.standard_normal((n_comp, d))).astype(np.float32)
+    g = _spectrum(d, spectrum)
+    centres = (rng.normal(0.0, centre_scale, size=(n_comp, d)) * g).astype(np.float32)
+    scales = (rng.lognormal(0.0, 0.5, size=(n_comp, d)) * g).astype(np.float32)
+    shifts = (0.5 * rng.standard_normal((n_comp, d)) * scales).astype(np.float32)
     base = np.empty((n, d), np.float32)
     for s, e in _chunks(n):
         comp = rng.integers(0, n_comp, size=e - s)
-        base[s:e] = centres[comp] + rng.standard_normal((e - s, d), dtype=np.float32)
+        base[s:e] = centres[comp] + scales[comp] * rng.standard_normal((e - s, d), dtype=np.float32)
     comp = rng.integers(0, n_comp, size=nq)
+    q = centres[comp] + scales[comp] * rng.standard_normal((nq, d), dtype=np.float32)
     shifted = np.arange(nq) >= nq // 2
-    q = centres[comp] + rng.standard_normal((nq, d), dtype=np.float32)
     q[shifted] += shifts[comp[shifted]]
     k = rng.choice(np.array([1, 10, 100], np.int32), size=nq)
     lo = np.maximum(32, k)

@@ -1,6 +1,8 @@
-"""Precision line: reduced-precision (FP16 / BF16) storage searched with FP32
-accumulation, then the exact FP32 rerank of the final pool (ANN_SEARCH_RERANK),
-against the oracle run on the same rounded rows and re-scored in float64.
+"""Precision line: reduced-precision (FP16 / BF16 / int8 with a per-row scale)
+storage searched with FP32 accumulation, then the exact FP32 rerank of the
+final pool (ANN_SEARCH_RERANK), against the oracle run on the same rounded
+rows and re-scored in float64.  The int8 codes and scales themselves are
+bit-exact against the oracle's quantiser.
 
 Bars: the traversal over rounded rows follows the fp32 agreement bar of the
 search tests (>= 99.9 % equal ids, 1e-5 relative distances); after the rerank
@@ -38,6 +40,12 @@ def _index(case, storage):
         stored = base.astype(np.float16)
         rows = stored.astype(np.float32)
         h = ann.ann_index_create(stored, case["graph"], case["medoid"], ann.F16, ann.L2, base_f32=base)
+    elif storage == "i8s":
+        n, d = base.shape
+        packed = _quantize(base)
+        rows = oracle.dequantize_i8s(*oracle.quantize_i8s(base))
+        h = ann.ann_index_create(packed, case["graph"], case["medoid"], ann.I8S, ann.L2, base_f32=base,
+                                 n=n, dim=d, degree=case["graph"].shape[1])
     else:
         rows = _bf16(base)
         stored = torch.from_numpy(base).to(torch.bfloat16)  # round to nearest even
@@ -51,6 +59,23 @@ def _index(case, storage):
     return h, rows
 
 
+def _quantize(base):
+    """Packed int8 rows from ann_quantize_i8s, checked byte for byte against
+    the oracle's codes and scales."""
+    n, d = base.shape
+    rb = ann.ann_i8s_row_bytes(d)
+    assert rb == 16 + (d + 15) // 16 * 16
+    packed = torch.full((n, rb), 0xAB, dtype=torch.uint8, device=DEV)
+    ann.ann_quantize_i8s(torch.from_numpy(base).to(DEV), n, d, packed)
+    torch.cuda.synchronize()
+    pk = packed.cpu().numpy()
+    codes, scales = oracle.quantize_i8s(base)
+    assert np.array_equal(pk[:, :4].copy().view(np.uint32)[:, 0], scales.view(np.uint32))
+    assert (pk[:, 4:16] == 0).all() and (pk[:, 16 + d:] == 0).all()
+    assert np.array_equal(pk[:, 16:16 + d].copy().view(np.int8), codes)
+    return packed
+
+
 def _run(h, q, L, k, flags):
     dq = torch.from_numpy(q).to(DEV)
     ids = torch.empty((len(q), k), dtype=torch.int32, device=DEV)
@@ -60,7 +85,7 @@ def _run(h, q, L, k, flags):
     return ids.cpu().numpy(), dd.cpu().numpy()
 
 
-@pytest.mark.parametrize("storage", ["f16", "bf16"])
+@pytest.mark.parametrize("storage", ["f16", "bf16", "i8s"])
 def test_reduced_storage_and_exact_rerank(case, storage):
     h, rows = _index(case, storage)
     try:
@@ -92,3 +117,25 @@ def test_rerank_needs_the_fp32_copy(case):
         assert e.value.status == ann.ERR_UNSUPPORTED
     finally:
         ann.ann_free_index(h)
+
+
+def test_i8s_inner_product_and_ragged_dim():
+    # unit rows, maximum inner product; dim 200 leaves a partly used last
+    # 16-code chunk (zero codes against a zero-extended query)
+    w = synth.ip_f32(n=12000, nq=200)
+    base = w["base"]
+    g, _ = oracle.build_graph(base, K=48, R=32)
+    med = oracle.medoid(base)
+    packed = _quantize(base)
+    h = ann.ann_index_create(packed, g, med, ann.I8S, ann.IP, n=len(base), dim=base.shape[1], degree=32)
+    try:
+        q = w["queries"]
+        ids, d = _run(h, q, 64, 10, 0)
+    finally:
+        ann.ann_free_index(h)
+    rows = oracle.dequantize_i8s(*oracle.quantize_i8s(base))
+    oi, od, _, _ = oracle.search(rows, g, q.astype(np.float64), med, 64, 10, metric=oracle.IP)
+    assert (ids == oi).mean() >= 0.999
+    ok = ids == oi
+    scale = np.linalg.norm(q.astype(np.float64), axis=1)[:, None].repeat(10, 1)  # |x| <= 1
+    assert (np.abs(d.astype(np.float64) - od)[ok] / scale[ok]).max() <= 1e-5

@@ -219,3 +219,30 @@ def test_f32_ip_parity():
     scale = np.linalg.norm(q.astype(np.float64), axis=1)  # |x| = 1
     assert st == ann.OK
     _f32_parity(ids, d, oi, od, truth, scale=scale)
+
+
+def test_visited_set_outgrows_both_global_tables():
+    # points on a line, x_i = i, each node linked to the next 64: a search
+    # from node 0 walks the chain and evaluates every node up to a little past
+    # the query.  At L = 16 the shared table (1,024 slots) and the first
+    # global table (4,096) overflow; the 4x larger one takes up to 12,288
+    # keys, so the query at 6,000 still finishes exactly and the one at
+    # 14,000 (all 14,000 nodes) fails with a capacity status and -1 ids.
+    n, R = 14000, 64
+    base = np.zeros((n, 4), np.float32)
+    base[:, 0] = np.arange(n)
+    nb = np.arange(n)[:, None] + 1 + np.arange(R)[None, :]
+    g = np.where(nb < n, nb, -1).astype(np.int32)
+    q = np.zeros((3, 4), np.float32)
+    q[:, 0] = [2000, 6000, 14000]
+    h = make_index(base, g, 0)
+    try:
+        ids, d, ev, hp, st = search(h, q, 10, 16, hash_bits=10)
+    finally:
+        ann.ann_free_index(h)
+    assert st == ann.ERR_CAPACITY
+    oi, od, oe, oh = oracle.search(base, g, q[:2].astype(np.float64), 0, 16, 10)
+    assert oe[1] > 3 * 4096 // 4  # past the first global table
+    assert np.array_equal(ids[:2], oi) and np.array_equal(ev[:2], oe) and np.array_equal(hp[:2], oh)
+    assert np.array_equal(d[:2], od.astype(np.float32))
+    assert (ids[2] == -1).all()
