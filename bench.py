@@ -348,6 +348,7 @@ class Runner:
                                          self.dists, 3, self.stream)
         self.tuned[L] = best
         return {"hash_bits": best.hash_bits, "stage_rows": best.stage_rows, "team": best.team,
+                "spill_bits": best.spill_bits,
                 "search_ms": ms}
 
     def select(self, q):
@@ -485,13 +486,18 @@ def cpu_baseline(W, L, entries=None, target_s=10.0, width=1, k=K_NN):
     oracle.search(base, g, allq[:probe], ent[:probe], L, k, W=width, metric=metric)
     per_q = (time.perf_counter() - t) / probe
     m = int(min(len(allq), max(probe, target_s / max(per_q, 1e-9))))
-    t = time.perf_counter()
-    ids, _, ev, _ = oracle.search(base, g, allq[:m], ent[:m], L, k, W=width, metric=metric)
-    dt = time.perf_counter() - t
-    return {"value": m / dt, "unit": "queries/s", "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"first {m} of the {len(allq)} evaluation queries at L={L}, W={width}, "
-                      f"entries as the GPU arm, float64 distances, one query per OpenMP thread "
-                      f"({dt:.1f} s)",
+    # repeat passes over the sample (at most 50) until about target_s went by
+    passes, done, t = 0, 0, time.perf_counter()
+    while True:
+        ids, _, ev, _ = oracle.search(base, g, allq[:m], ent[:m], L, k, W=width, metric=metric)
+        passes, done = passes + 1, done + m
+        dt = time.perf_counter() - t
+        if dt >= 0.5 * target_s or passes >= 50:
+            break
+    return {"value": done / dt, "unit": "queries/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{passes} pass(es) over the first {m} of the {len(allq)} evaluation queries at "
+                      f"L={L}, W={width}, entries as the GPU arm, float64 distances, one query per "
+                      f"OpenMP thread ({dt:.1f} s)",
             "recall@10_sample": recall(ids, W["gt"][:m]), "evals_per_query": float(ev.mean())}
 
 
@@ -595,7 +601,7 @@ def batch_report(W, torch, ann, args, dev):
     for b0 in range(0, nq, B):
         sl = slice(b0, b0 + B)
         pb = ann.search_params(100, 512, W=1, hash_bits=best.hash_bits, stage_rows=best.stage_rows,
-                               team=best.team, d_k=kq[sl], d_L=Lq[sl])
+                               team=best.team, spill_bits=best.spill_bits, d_k=kq[sl], d_L=Lq[sl])
         a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         ann.ann_search_batch(W["h"], q[sl], B, None, pb, ids[sl], dd[sl], None, stream)
@@ -606,7 +612,7 @@ def batch_report(W, torch, ann, args, dev):
     ib = torch.empty((B, 100), dtype=torch.int32, device=dev)
     db = torch.empty((B, 100), dtype=torch.float32, device=dev)
     pp = ann.search_params(100, 512, W=1, hash_bits=best.hash_bits, stage_rows=best.stage_rows,
-                           team=best.team, d_k=kb, d_L=lb)
+                           team=best.team, spill_bits=best.spill_bits, d_k=kb, d_L=lb)
     plan = ann.ann_plan_create(W["h"], qb, B, ann.ENTRY_MEDOID, 0, pp, None, ib, db)
     try:
         for _ in range(100):
@@ -620,7 +626,8 @@ def batch_report(W, torch, ann, args, dev):
         ann.ann_plan_free(plan)
     return {"qps_one_launch": qps, "recall_at_own_k": rec, "queries": nq,
             "evals_per_query": float(s[:, 0].mean()), "hops_per_query": float(s[:, 1].mean()),
-            "tuned": {"hash_bits": best.hash_bits, "stage_rows": best.stage_rows, "team": best.team},
+            "tuned": {"hash_bits": best.hash_bits, "stage_rows": best.stage_rows, "team": best.team,
+                      "spill_bits": best.spill_bits},
             "batch": B, "batch_latency_ms": {"p50": float(np.percentile(lat, 50)),
                                              "p99": float(np.percentile(lat, 99))},
             "plan_latency_ms": {"p50": float(np.percentile(lat_plan, 50)),

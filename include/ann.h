@@ -114,6 +114,10 @@ typedef struct {
  *             1, 2, 4, 8, 16 or 32.  Speed only for uint8 data; for float
  *             data it sets the FP32 summation order, so distances may differ
  *             in the last bits between teams
+ *   spill_bits log2 of the slots of the first global visited table a query
+ *             moves to when its shared table fills (the second one has four
+ *             times as many), 0 = chosen from L; 10..16.  Speed only, unless
+ *             a query outgrows both tables (ANN_ERR_CAPACITY)
  *   flags     ANN_SEARCH_* bits.  ANN_SEARCH_RERANK: after the search, every
  *             id of the final pool (L entries) is re-scored exactly from the
  *             index's fp32 copy of the rows (ann_index_desc.base_f32; without
@@ -133,6 +137,7 @@ typedef struct {
     int32_t hash_bits;
     int32_t stage_rows;
     int32_t team;
+    int32_t spill_bits;
     uint32_t flags;
     const int32_t *d_k;
     const int32_t *d_L;
@@ -240,9 +245,10 @@ ann_status ann_plan_free(ann_plan *plan);
 
 /*
  * Time ann_search_batch over the given batch for visited-table sizes around
- * and below the default (hash_bits), gather round sizes (stage_rows 4, 8, 16)
- * and distance team sizes (team 4, 8, 16, 32 where a team has at least one
- * 16-byte chunk of the row per lane), reps runs each after one warm-up, and
+ * and below the default (hash_bits), gather round sizes (stage_rows 4, 8, 16),
+ * distance team sizes (team 2 to 32 where a lane gets 1 to 16 16-byte chunks
+ * of the row) and first spill-table sizes (spill_bits up to two either side
+ * of the default), one after the other, reps runs each after one warm-up, and
  * return in *best the copy of *p with the fastest combination (*best_ms: its
  * mean time).  The visited set stays exact (shared table plus global spill)
  * and the gather order does not enter any result; the team size only moves

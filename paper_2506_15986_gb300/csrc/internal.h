@@ -68,6 +68,10 @@ ann_status launch_search(ann_index *idx, const SearchLaunch &L, cudaStream_t s);
 // two >= 4 that leaves each lane at most four 16-byte chunks of a row.
 int default_team(int rowbytes);
 
+// log2 slots of the first global visited table when ann_search_params.
+// spill_bits is 0: 40 evaluations per pool slot below 3/4 load, 12..15.
+int default_spill_bits(int L);
+
 // Scratch bytes launch_search needs for `teams` teams at the given params.
 size_t search_scratch_bytes(int teams, int spill_bits);
 

@@ -168,6 +168,18 @@ ann_status ann_autotune(ann_index *idx, const void *d_queries, int64_t nq, const
         c.team = g;
         ok = trial(c);
     }
+    // stage 3: first spill tables one and two sizes either side of the
+    // default at the best so far (larger: fewer collisions; smaller: less to
+    // clear; the second table takes the tail)
+    const ann_search_params b2 = bp;
+    const int sb0 = b2.spill_bits > 0 ? b2.spill_bits : ann::default_spill_bits(p->L);
+    for (int sb = sb0 - 2; ok && sb <= sb0 + 2; ++sb) {
+        if (sb < 10 || sb > 16 || sb == sb0)
+            continue;
+        ann_search_params c = b2;
+        c.spill_bits = sb;
+        ok = trial(c);
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaSetDevice(prev);

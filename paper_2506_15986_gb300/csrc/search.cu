@@ -62,7 +62,7 @@ struct SearchArgs {
     uint32_t *spill;
     int hash_bits, spill_bits;
     // per-warp shared-memory layout (byte offsets)
-    int off_sel, off_q, off_stage, off_pool, off_ptmp, off_cbuf, off_cids, off_hash, per_warp;
+    int off_sel, off_q, off_stage, off_pool, off_ptop, off_cbuf, off_hash, per_warp;
     int stage_rows, stage_stride;
     int team_lg;  // log2 of the lanes computing one distance
 };
@@ -117,31 +117,34 @@ template <int NS>
 __device__ __forceinline__ void visit_slots(uint32_t *tab, int bits, const int32_t (&ids)[NS], int (&res)[NS])
 {
     const uint32_t mask = (1u << bits) - 1u;
-    uint32_t h[NS];
+    uint32_t h[NS], key[NS], old[NS];
+    // issue every compare-and-swap before looking at any result
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        key[s] = static_cast<uint32_t>(ids[s]) + 1u;
+        h[s] = hash_slot(key[s], bits);
+        old[s] = ids[s] >= 0 ? atomicCAS(&tab[h[s]], 0u, key[s]) : 0u;
+    }
     bool more = false;
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
-        res[s] = 0;
-        h[s] = 0;
-        if (ids[s] >= 0) {
-            const uint32_t key = static_cast<uint32_t>(ids[s]) + 1u;
-            h[s] = hash_slot(key, bits);
-            const uint32_t old = atomicCAS(&tab[h[s]], 0u, key);
-            res[s] = old == 0u ? 1 : (old == key ? 0 : 2);
-            more |= res[s] == 2;
-        }
+        res[s] = ids[s] < 0 ? 0 : (old[s] == 0u ? 1 : (old[s] == key[s] ? 0 : 2));
+        more |= res[s] == 2;
     }
     for (uint32_t p = 1; p <= mask && more; ++p) {
-        more = false;
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
             if (res[s] == 2) {
-                const uint32_t key = static_cast<uint32_t>(ids[s]) + 1u;
                 h[s] = (h[s] + 1u) & mask;
-                const uint32_t old = atomicCAS(&tab[h[s]], 0u, key);
-                res[s] = old == 0u ? 1 : (old == key ? 0 : 2);
-                more |= res[s] == 2;
+                old[s] = atomicCAS(&tab[h[s]], 0u, key[s]);
             }
+        }
+        more = false;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            if (res[s] == 2)
+                res[s] = old[s] == 0u ? 1 : (old[s] == key[s] ? 0 : 2);
+            more |= res[s] == 2;
         }
     }
 #pragma unroll
@@ -313,9 +316,8 @@ __global__ void __launch_bounds__(32 * kSearchWarps) beam_search_kernel(const Se
     uint8_t *qbuf = my + a.off_q;
     uint8_t *stage = my + a.off_stage;
     uint64_t *pool = reinterpret_cast<uint64_t *>(my + a.off_pool);
-    uint64_t *ptmp = reinterpret_cast<uint64_t *>(my + a.off_ptmp);
+    uint64_t *ptop = reinterpret_cast<uint64_t *>(my + a.off_ptop);  // W keys for the prediction
     uint64_t *cbuf = reinterpret_cast<uint64_t *>(my + a.off_cbuf);
-    int32_t *cids = reinterpret_cast<int32_t *>(my + a.off_cids);
     uint32_t *htab = reinterpret_cast<uint32_t *>(my + a.off_hash);
     const int team = blockIdx.x * kSearchWarps + wid;
     // two global spill tables per team: 2^spill_bits slots, then one four
@@ -377,7 +379,7 @@ __global__ void __launch_bounds__(32 * kSearchWarps) beam_search_kernel(const Se
             __syncwarp();
             if (lane == 0) {
                 visit(htab, a.hash_bits, false, gtab1, a.spill_bits, entry);
-                cids[0] = entry;
+                cbuf[0] = static_cast<uint64_t>(entry) << 1;
             }
             used = 1;
             evals = 1;
@@ -387,7 +389,8 @@ __global__ void __launch_bounds__(32 * kSearchWarps) beam_search_kernel(const Se
         __syncwarp();
 
         while (!failed) {
-            // ---- evaluate the nc candidates in cids[]; the survivors end sorted
+            // ---- evaluate the nc candidates in cbuf[] (their ids in the key
+            // layout, distance bits 0); the survivors end sorted
             // in cbuf[0, m)
             int m = 0;
             if (nc > 0) {
@@ -398,7 +401,7 @@ __global__ void __launch_bounds__(32 * kSearchWarps) beam_search_kernel(const Se
                     __syncwarp();
                     for (int j = lane; j < ch; j += 32)
                         bulk_g2s(stage + j * a.stage_stride,
-                                 a.base + static_cast<size_t>(cids[c0 + j]) * a.rowbytes,
+                                 a.base + static_cast<size_t>(key_id(cbuf[c0 + j])) * a.rowbytes,
                                  a.rowbytes, bar);
                     bool ok = mbar_wait_bounded(bar, phase, kTimeoutIters);
                     if (!__all_sync(kFull, ok)) {
@@ -416,7 +419,7 @@ __global__ void __launch_bounds__(32 * kSearchWarps) beam_search_kernel(const Se
                         const uint32_t bits = group_distance<DT, MT>(stage + min(r, ch - 1) * a.stage_stride,
                                                                      qbuf, a.rowbytes, sub, 1 << a.team_lg);
                         if (r < ch && sub == 0)
-                            cbuf[c0 + r] = make_key(bits, cids[c0 + r]);
+                            cbuf[c0 + r] = make_key(bits, key_id(cbuf[c0 + r]));
                     }
                     __syncwarp();
                     fence_proxy_async_smem();  // stage reads done before the next bulk writes
@@ -487,15 +490,15 @@ __global__ void __launch_bounds__(32 * kSearchWarps) beam_search_kernel(const Se
                     const unsigned um = __ballot_sync(kFull, un);
                     const int g = nf + __popc(um & lanemask_lt());
                     if (un && g < a.W)
-                        ptmp[g] = pool[i];  // ptmp is free until the merge
+                        ptop[g] = pool[i];
                     nf = min(a.W, nf + __popc(um));
                 }
                 __syncwarp();
                 const int mw = min(m, a.W);
                 int i = 0, j = 0, np = 0;
                 for (; np < a.W && (i < nf || j < mw); ++np) {
-                    const bool from_pool = j >= mw || (i < nf && ptmp[i] < cbuf[j]);
-                    const uint64_t v = from_pool ? ptmp[i++] : cbuf[j++];
+                    const bool from_pool = j >= mw || (i < nf && ptop[i] < cbuf[j]);
+                    const uint64_t v = from_pool ? ptop[i++] : cbuf[j++];
                     if (lane == 0)
                         pred[np] = key_id(v);
                 }
@@ -509,25 +512,36 @@ __global__ void __launch_bounds__(32 * kSearchWarps) beam_search_kernel(const Se
                 }
             }
 
-            // ---- merge the survivors into the pool by rank
+            // ---- merge the survivors into the pool by rank, in place: the
+            // survivors' ranks come from the unmodified pool; pool entries move
+            // right by the number of smaller survivors, 32 at a time from the
+            // back, so that none is overwritten before it is read
             if (m > 0) {
-                const int p0 = count_less(pool, cnt, cbuf[0]);
-                const int mv = cnt - p0;
-                for (int i = lane; i < mv; i += 32)
-                    ptmp[i] = pool[p0 + i];
+                int dst[kSlots];
+#pragma unroll
+                for (int r = 0; r < kSlots; ++r) {
+                    const int j = lane + 32 * r;
+                    dst[r] = j < m ? j + count_less(pool, cnt, cbuf[j]) : Lq;
+                }
+                const int p0 = __shfl_sync(kFull, dst[0], 0);  // rank of the best survivor
                 __syncwarp();
-                for (int i = lane; i < mv; i += 32) {
-                    const uint64_t v = ptmp[i];
-                    const int np = p0 + i + count_less(cbuf, m, key_plain(v));
+                for (int b = cnt > p0 ? p0 + (cnt - 1 - p0) / 32 * 32 : p0 - 32; b >= p0; b -= 32) {
+                    const int i = b + lane;
+                    uint64_t v = 0;
+                    int np = Lq;
+                    if (i < cnt) {
+                        v = pool[i];
+                        np = i + count_less(cbuf, m, key_plain(v));
+                    }
+                    __syncwarp();
                     if (np < Lq)
                         pool[np] = v;
+                    __syncwarp();
                 }
-                for (int j = lane; j < m; j += 32) {
-                    const uint64_t v = cbuf[j];
-                    const int np = p0 + j + count_less(ptmp, mv, v);
-                    if (np < Lq)
-                        pool[np] = v;
-                }
+#pragma unroll
+                for (int r = 0; r < kSlots; ++r)
+                    if (dst[r] < Lq)
+                        pool[dst[r]] = cbuf[lane + 32 * r];
                 __syncwarp();
                 cnt = min(Lq, cnt + m);
                 cursor = min(cursor, p0);
@@ -618,7 +632,7 @@ __global__ void __launch_bounds__(32 * kSearchWarps) beam_search_kernel(const Se
                 bad |= (res[s] < 0);
                 const unsigned nm = __ballot_sync(kFull, res[s] == 1);
                 if (res[s] == 1) {
-                    cids[nc + __popc(nm & lanemask_lt())] = vid[s];
+                    cbuf[nc + __popc(nm & lanemask_lt())] = static_cast<uint64_t>(static_cast<uint32_t>(vid[s])) << 1;
                     if (vid[s] == target)
                         found = true;
                 }
@@ -792,6 +806,14 @@ int default_team(int rowbytes)
     return G;
 }
 
+int default_spill_bits(int L)
+{
+    int sb = 12;
+    while ((1 << sb) * 3 / 4 < 40 * L && sb < 15)
+        ++sb;
+    return sb;
+}
+
 size_t search_scratch_bytes(int teams, int spill_bits)
 {
     return 256 + static_cast<size_t>(teams) * (static_cast<size_t>(20) << spill_bits);
@@ -841,9 +863,9 @@ ann_status launch_search(ann_index *idx, const SearchLaunch &L, cudaStream_t s)
     // (about 3x the typical count), small enough to stay mostly L2-resident
     // and cheap to clear when a query starts spilling; the second holds four
     // times more for the tail
-    int sb = 12;
-    while ((1 << sb) * 3 / 4 < 40 * p->L && sb < 15)
-        ++sb;
+    int sb = default_spill_bits(p->L);
+    if (p->spill_bits > 0)
+        sb = p->spill_bits;
     a.spill_bits = sb;
 
     const int maxc = p->W * idx->degree;
@@ -862,10 +884,10 @@ ann_status launch_search(ann_index *idx, const SearchLaunch &L, cudaStream_t s)
         while (s16 % G != 0 || ((s16 / G) & 1) == 0)
             ++s16;
     a.stage_stride = s16 * 16;
-    // Most steps find far fewer new neighbours than W * R (about 9 of 32 on
-    // average), so 16 rows per gather round keep shared memory per team small
-    // (more teams per SM); at most 48 KB staged at once, which also keeps one
-    // mbarrier phase's byte count far below its 2^20 limit.
+    // Most steps find far fewer new neighbours than W * R (about 30 % of
+    // them), so a small staging area filled in rounds keeps shared memory per
+    // team small (more teams per SM); at most 48 KB staged at once, which also
+    // keeps one mbarrier phase's byte count far below its 2^20 limit.
     a.stage_rows = std::max(1, std::min({maxc, p->stage_rows > 0 ? p->stage_rows : 16, 49152 / a.stage_stride}));
 
     size_t off = 16;  // mbarrier
@@ -877,12 +899,10 @@ ann_status launch_search(ann_index *idx, const SearchLaunch &L, cudaStream_t s)
     off = align_up(off + static_cast<size_t>(a.stage_rows) * a.stage_stride, 16);
     a.off_pool = static_cast<int>(off);
     off = align_up(off + 8 * static_cast<size_t>(p->L), 16);
-    a.off_ptmp = static_cast<int>(off);
-    off = align_up(off + 8 * static_cast<size_t>(p->L), 16);
+    a.off_ptop = static_cast<int>(off);
+    off = align_up(off + 8 * ANN_MAX_W, 16);
     a.off_cbuf = static_cast<int>(off);
     off = align_up(off + 8 * ANN_MAX_STEP_CAND, 16);
-    a.off_cids = static_cast<int>(off);
-    off = align_up(off + 4 * ANN_MAX_STEP_CAND, 16);
     a.off_hash = static_cast<int>(off);
     off = align_up(off + (static_cast<size_t>(4) << hb), 128);
     a.per_warp = static_cast<int>(off);
@@ -899,6 +919,7 @@ ann_status launch_search(ann_index *idx, const SearchLaunch &L, cudaStream_t s)
     teams = static_cast<int>(std::min<long long>(teams, L.nq));
     if (teams < 1)
         return ANN_OK;
+    teams = (teams + kSearchWarps - 1) / kSearchWarps * kSearchWarps;  // whole CTAs
 
     // scratch: work counter, then two spill tables per team
     const size_t need = search_scratch_bytes(teams, a.spill_bits);
