@@ -105,7 +105,8 @@ typedef struct {
  *   L         pool size, 1 <= L <= ANN_MAX_L; the maximum when d_L is given
  *   W         pool entries expanded per step, 1..ANN_MAX_W, W*degree <= 128
  *   hash_bits log2 of the per-query shared-memory visited-table capacity,
- *             0 = chosen from L; 8..15
+ *             0 = chosen from L; 8..15; -1 = no shared table (the visited set
+ *             lives in the global spill tables from the first step)
  *   stage_rows neighbour rows gathered into shared memory per round, 0 =
  *             chosen from the row size; 1..32.  hash_bits and stage_rows change
  *             speed only, never results (see ann_autotune)
@@ -245,7 +246,8 @@ ann_status ann_plan_free(ann_plan *plan);
 
 /*
  * Time ann_search_batch over the given batch for visited-table sizes around
- * and below the default (hash_bits), gather round sizes (stage_rows 4, 8, 16),
+ * and below the default and no shared table (hash_bits), gather round sizes
+ * (stage_rows 4, 8, 16),
  * distance team sizes (team 2 to 32 where a lane gets 1 to 16 16-byte chunks
  * of the row) and first spill-table sizes (spill_bits up to two either side
  * of the default), one after the other, reps runs each after one warm-up, and

@@ -382,7 +382,8 @@ ann_status ann_search_batch(ann_index *idx, const void *d_queries, int64_t nq, c
         return ANN_ERR_INVALID_ARG;
     if (p->L < 1 || p->L > ANN_MAX_L || p->k < 1 || p->k > p->L || p->W < 1 || p->W > ANN_MAX_W ||
         p->W * idx->degree > ANN_MAX_STEP_CAND ||
-        (p->hash_bits != 0 && (p->hash_bits < 8 || p->hash_bits > 15)) || p->stage_rows < 0 ||
+        (p->hash_bits != 0 && p->hash_bits != -1 && (p->hash_bits < 8 || p->hash_bits > 15)) ||
+        p->stage_rows < 0 ||
         p->stage_rows > 32 || p->team < 0 || p->team > 32 || (p->team & (p->team - 1)) != 0 ||
         (p->spill_bits != 0 && (p->spill_bits < 10 || p->spill_bits > 16)))
         return ANN_ERR_INVALID_ARG;

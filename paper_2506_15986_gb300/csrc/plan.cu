@@ -108,7 +108,7 @@ ann_status ann_autotune(ann_index *idx, const void *d_queries, int64_t nq, const
     int hb0 = 10;
     while ((1 << hb0) * 3 / 4 < 12 * p->L && hb0 < 13)
         ++hb0;
-    std::vector<int> hbs;
+    std::vector<int> hbs = {-1};  // -1: no shared table
     for (int hb = hb0 - 3; hb <= hb0; ++hb)
         if (hb >= 8 && hb <= 15)
             hbs.push_back(hb);

@@ -331,7 +331,9 @@ __global__ void __launch_bounds__(32 * kSearchWarps) beam_search_kernel(const Se
     }
     __syncwarp();
     uint32_t phase = 0;
-    const int hcap = 1 << a.hash_bits;
+    // hash_bits < 0: no shared table, the visited set starts in the global one
+    const bool shared_tab = a.hash_bits > 0;
+    const int hcap = shared_tab ? 1 << a.hash_bits : 0;
     const int hlimit = hcap * 3 / 4;
 
     for (;;) {
@@ -358,7 +360,8 @@ __global__ void __launch_bounds__(32 * kSearchWarps) beam_search_kernel(const Se
         int cnt = 0, cursor = 0, evals = 0, hops = 0;
         // visited set: level 0 = the shared table, 1 and 2 = the global ones;
         // used = keys in the current table, limit = its 3/4 load
-        int level = 0, used = 0, limit = hlimit, gbits = a.spill_bits;
+        int level = shared_tab ? 0 : 1, used = 0, gbits = a.spill_bits;
+        int limit = shared_tab ? hlimit : (1 << a.spill_bits) * 3 / 4;
         uint32_t *gtab = gtab1;
         int32_t *pred = sel + ANN_MAX_W;  // predicted ids of the next selection
         int npred = 0;
@@ -376,9 +379,12 @@ __global__ void __launch_bounds__(32 * kSearchWarps) beam_search_kernel(const Se
                 *reinterpret_cast<float *>(qbuf + o) = 0.f;
             for (int o = lane; o < hcap / 4; o += 32)
                 reinterpret_cast<uint4 *>(htab)[o] = make_uint4(0u, 0u, 0u, 0u);
+            if (!shared_tab)
+                for (int o = lane; o < (1 << a.spill_bits) / 4; o += 32)
+                    reinterpret_cast<uint4 *>(gtab1)[o] = make_uint4(0u, 0u, 0u, 0u);
             __syncwarp();
             if (lane == 0) {
-                visit(htab, a.hash_bits, false, gtab1, a.spill_bits, entry);
+                visit(htab, a.hash_bits, !shared_tab, gtab1, a.spill_bits, entry);
                 cbuf[0] = static_cast<uint64_t>(entry) << 1;
             }
             used = 1;
@@ -849,7 +855,7 @@ ann_status launch_search(ann_index *idx, const SearchLaunch &L, cudaStream_t s)
     a.out_stats = L.stats;
     a.status = idx->status_sink ? idx->status_sink : idx->d_status;
 
-    int hb = p->hash_bits;
+    int hb = p->hash_bits;  // -1: no shared table
     if (hb == 0) {
         // searches evaluate about 10-16 nodes per pool slot; size the shared
         // table for 12 per slot below its 3/4 load limit (the exact global
@@ -904,7 +910,7 @@ ann_status launch_search(ann_index *idx, const SearchLaunch &L, cudaStream_t s)
     a.off_cbuf = static_cast<int>(off);
     off = align_up(off + 8 * ANN_MAX_STEP_CAND, 16);
     a.off_hash = static_cast<int>(off);
-    off = align_up(off + (static_cast<size_t>(4) << hb), 128);
+    off = align_up(off + (hb > 0 ? static_cast<size_t>(4) << hb : 0), 128);
     a.per_warp = static_cast<int>(off);
     const size_t smem = off * kSearchWarps;
 

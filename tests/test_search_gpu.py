@@ -111,14 +111,14 @@ def test_c1_team_sizes_bit_exact(c1, team, stage_rows):
     assert np.array_equal(d, od.astype(np.int64).astype(np.int32))
 
 
-@pytest.mark.parametrize("L,spill_bits", [(128, 0), (512, 10)])
-def test_c1_spill_to_global_table_stays_exact(c1, L, spill_bits):
+@pytest.mark.parametrize("L,spill_bits,hash_bits", [(128, 0, 8), (512, 10, 8), (128, 0, -1), (512, 10, -1)])
+def test_c1_spill_to_global_table_stays_exact(c1, L, spill_bits, hash_bits):
     # hash_bits=8: 192 shared slots, far fewer than the evaluations, so the
     # exact global spill table carries most of the visited set; with
     # spill_bits=10 at L=512 most queries pass 768 evaluations and move on to
     # the second, 4x larger table
     q = c1["queries"]
-    ids, d, ev, hp, st = search(c1["h"], q, 10, L, hash_bits=8, spill_bits=spill_bits)
+    ids, d, ev, hp, st = search(c1["h"], q, 10, L, hash_bits=hash_bits, spill_bits=spill_bits)
     oi, od, oe, oh = _oracle(c1, q, L, 10)
     assert st == ann.OK
     assert (oe > 192).mean() > 0.8  # most queries outgrow the shared table
@@ -168,7 +168,7 @@ def test_empty_batch_and_bad_device_inputs(c1):
     assert (ids[1] == -1).all() and (ids[0] >= 0).all()
     assert ann.ann_sync_status(c1["h"]) == ann.OK  # cleared by the read
     # host-side parameter checks return before any launch
-    for kw in (dict(team=3), dict(team=64), dict(stage_rows=33), dict(W=5), dict(hash_bits=7),
+    for kw in (dict(team=3), dict(team=64), dict(stage_rows=33), dict(W=5), dict(hash_bits=7), dict(hash_bits=-2),
                dict(spill_bits=9), dict(spill_bits=17)):
         with pytest.raises(ann.AnnError) as e:
             search(c1["h"], q[:4], 10, 64, **kw)
