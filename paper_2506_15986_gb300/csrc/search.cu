@@ -44,6 +44,7 @@ struct SearchArgs {
     const int32_t *graph;
     int64_t n;
     int dim, R, rowbytes;
+    int R_inv;  // ceil(2^16 / R): (t * R_inv) >> 16 == t / R for all t < 128, 1 <= R <= 128
     const uint8_t *queries;
     int qbytes;
     int qpad;  // zero bytes after the query row in shared memory
@@ -514,7 +515,8 @@ __global__ void __launch_bounds__(32 * kSearchWarps) beam_search_kernel(const Se
 #pragma unroll
                 for (int r = 0; r < kSlots; ++r) {
                     const int t = lane + 32 * r;
-                    nxt[r] = t < tp ? __ldg(a.graph + static_cast<int64_t>(pred[t / a.R]) * a.R + t % a.R) : -1;
+                    const int e = (t * a.R_inv) >> 16;  // t / R
+                    nxt[r] = t < tp ? __ldg(a.graph + static_cast<int64_t>(pred[e]) * a.R + (t - e * a.R)) : -1;
                 }
             }
 
@@ -590,7 +592,9 @@ __global__ void __launch_bounds__(32 * kSearchWarps) beam_search_kernel(const Se
             for (int r = 0; r < kSlots; ++r) {
                 const int t = lane + 32 * r;
                 cur[r] = hit ? nxt[r]
-                             : (t < total ? __ldg(a.graph + static_cast<int64_t>(sel[t / a.R]) * a.R + t % a.R) : -1);
+                             : (t < total ? __ldg(a.graph + static_cast<int64_t>(sel[(t * a.R_inv) >> 16]) * a.R +
+                                                   (t - ((t * a.R_inv) >> 16) * a.R))
+                                          : -1);
             }
 
             // ---- neighbours of the selected entries: visited test, compaction
@@ -834,6 +838,7 @@ ann_status launch_search(ann_index *idx, const SearchLaunch &L, cudaStream_t s)
     a.n = idx->n;
     a.dim = idx->dim;
     a.R = idx->degree;
+    a.R_inv = ((1 << 16) + a.R - 1) / a.R;
     a.rowbytes = idx->rowbytes;
     a.queries = static_cast<const uint8_t *>(L.queries);
     a.qbytes = L.qbytes;
