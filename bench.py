@@ -95,6 +95,27 @@ WORKLOADS = {
 }
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one headline
+# search launch, from an ncu capture of this bench's timed steps; it counts
+# only while the search kernel's sources are the ones it was taken on.
+MEASURED_TRAFFIC = {
+    # profiles/beam_search_shift1M.md: 3.84 GB read + 1.05 GB written per launch
+    "shift": dict(digest="2fa50803eb87b524", entry="exhaustive", L=96, nq=10_000, spill_bits=14,
+                  bytes=3.84e9 + 1.05e9),
+}
+
+
+def kernel_digest():
+    """Digest of the sources that define the search kernel."""
+    import hashlib
+    h = hashlib.sha1()
+    for rel in ("paper_2506_15986_gb300/csrc/search.cu", "paper_2506_15986_gb300/csrc/device_util.cuh",
+                "paper_2506_15986_gb300/csrc/internal.h", "include/ann.h"):
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -413,9 +434,10 @@ def sweep(run, torch, ann, W, targets):
     return Lstar, out, per
 
 
-def timed(run, torch, ann, args, L, world, dev):
+def timed(run, torch, ann, args, L, world, dev, nvtx=None):
     """The timed region: W warm-up steps, then K steps bracketed by a barrier
-    and a device synchronize; per-launch events around the search kernel."""
+    and a device synchronize; per-launch events around the search kernel.
+    nvtx names an NVTX range around the timed steps (for a profiler filter)."""
     for _ in range(args.warmup):
         run.step(L)
     if world > 1:
@@ -427,6 +449,8 @@ def timed(run, torch, ann, args, L, world, dev):
     with Clocks(dev.index or 0) as clk:
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
+        if nvtx:
+            torch.cuda.nvtx.range_push(nvtx)
         t0.record(run.stream)
         for i in range(args.steps):
             e = run.select(q)
@@ -434,6 +458,8 @@ def timed(run, torch, ann, args, L, world, dev):
             run.search(q, e, L)
             ev[2 * i + 1].record(run.stream)
         t1.record(run.stream)
+        if nvtx:
+            torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
     if world > 1:
         import torch.distributed as distd
@@ -664,7 +690,7 @@ def run_gpu(args):
     learned_modes = [m for m in res if m != "medoid"]
     head = max(learned_modes, key=lambda m: probe[m]) if learned_modes else "medoid"
     R = res[head]
-    total_ms, search_ms, clocks = timed(R["run"], torch, ann, args, R["L"], world, dev)
+    total_ms, search_ms, clocks = timed(R["run"], torch, ann, args, R["L"], world, dev, nvtx="headline")
     value = world * R["run"].nq * args.steps / (total_ms / 1e3)
     others = {}
     for mode, r in res.items():
@@ -681,6 +707,11 @@ def run_gpu(args):
     batching = batch_report(W, torch, ann, args, dev) if spec.get("batching") else None
     peak, peak_kind = peaks()
     achieved = R["alg_bytes"] / (search_ms / 1e3) / 1e9
+    mt = MEASURED_TRAFFIC.get(args.workload)
+    traffic = None
+    if mt and mt["digest"] == kernel_digest() and mt["entry"] == head and mt["L"] == R["L"] \
+            and mt["nq"] == R["run"].nq and (R["tune"] or {}).get("spill_bits") == mt["spill_bits"]:
+        traffic = mt["bytes"]
     out = None
     if rank == 0:
         cpu = None if args.no_cpu else cpu_baseline(W, R["L"], R["entries"], width=args.W)
@@ -706,7 +737,8 @@ def run_gpu(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "u8" if W["dt"] == ann.U8 else "f32", "data": "synthetic", "config": cfg,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": traffic,
+                         "traffic_kernel_digest": kernel_digest(),
                          "kernel": "beam_search_kernel", "peak_kind": f"{peak_kind} copy bandwidth",
                          "alg_bytes_per_launch": R["alg_bytes"], "launch_ms": search_ms},
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,

@@ -247,7 +247,7 @@ ann_status ann_plan_free(ann_plan *plan);
 /*
  * Time ann_search_batch over the given batch for visited-table sizes around
  * and below the default and no shared table (hash_bits), gather round sizes
- * (stage_rows 4, 8, 16),
+ * (stage_rows 4, 8, 12, 16),
  * distance team sizes (team 2 to 32 where a lane gets 1 to 16 16-byte chunks
  * of the row) and first spill-table sizes (spill_bits up to two either side
  * of the default), one after the other, reps runs each after one warm-up, and

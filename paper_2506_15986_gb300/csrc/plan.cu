@@ -112,7 +112,7 @@ ann_status ann_autotune(ann_index *idx, const void *d_queries, int64_t nq, const
     for (int hb = hb0 - 3; hb <= hb0; ++hb)
         if (hb >= 8 && hb <= 15)
             hbs.push_back(hb);
-    const int srs[] = {4, 8, 16};
+    const int srs[] = {4, 8, 12, 16};
     float bms = 1e30f;
     ann_search_params bp = *p;
     ann_status st = ANN_OK;

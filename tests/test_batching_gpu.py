@@ -100,7 +100,7 @@ def test_autotune_keeps_results(case):
     ann.ann_search_batch(case["h"], q, nq, None, p, ids, dd)
     ref = ids.clone(), dd.clone()
     best, ms = ann.ann_autotune(case["h"], q, nq, None, p, ids, dd, reps=2)
-    assert ms > 0 and (best.hash_bits >= 8 or best.hash_bits == -1) and best.stage_rows in (4, 8, 16)
+    assert ms > 0 and (best.hash_bits >= 8 or best.hash_bits == -1) and best.stage_rows in (4, 8, 12, 16)
     assert best.team in (2, 4, 8, 16, 32) and best.spill_bits in (0, 10, 11, 12, 13, 14, 15, 16)
     ann.ann_search_batch(case["h"], q, nq, None, best, ids, dd)
     torch.cuda.synchronize()
