@@ -80,9 +80,9 @@ __device__ __forceinline__ int visit(uint32_t *htab, int hbits, bool global_mode
                                      int gbits, int32_t id)
 {
     const uint32_t key = static_cast<uint32_t>(id) + 1u;
-    const uint32_t hmask = (1u << hbits) - 1u;
-    uint32_t h = hash_slot(key, hbits);
     if (!global_mode) {
+        const uint32_t hmask = (1u << hbits) - 1u;
+        uint32_t h = hash_slot(key, hbits);
         for (uint32_t p = 0; p <= hmask; ++p) {
             uint32_t old = atomicCAS(&htab[h], 0u, key);
             if (old == 0u)
@@ -93,7 +93,8 @@ __device__ __forceinline__ int visit(uint32_t *htab, int hbits, bool global_mode
         }
         return -1;
     }
-    // global mode: the shared table's entries were moved to the global table
+    // global mode: the set lives in a global table (after a spill, or from
+    // the start when there is no shared table)
     const uint32_t gmask = (1u << gbits) - 1u;
     uint32_t g = hash_slot(key, gbits);
     for (uint32_t p = 0; p <= gmask; ++p) {
