@@ -88,10 +88,11 @@ WORKLOADS = {
         desc=("batch_f32 (scaled from 10M to 2M base rows so that the exact-kNN graph builds in "
               "seconds): N=2,000,000 fp32 d=96 (10,000-component anisotropic mixture, variance "
               "spectrum (1+i)^-1), 100,000 queries, half shifted, per-query k in {1,10,100} and L "
-              "uniform in [max(32,k),512], one persistent launch; per-batch latency over batches of "
-              "1,000"),
-        gen="batch_f32", n=2_000_000, nq=100_000, n_train=0, dim=96, R=32, metric="l2",
-        dtype="f32", hubs=0, learned=False, targets=[0.95], batching=True),
+              "uniform in [max(32,k),512], one persistent launch; 16,384 k-means hubs, BF16 query "
+              "tower 96-256-64 trained on 100,000 labelled queries; learned vs medoid entry; "
+              "per-batch latency over batches of 1,000"),
+        gen="batch_f32", n=2_000_000, nq=100_000, n_train=100_000, dim=96, R=32, metric="l2",
+        dtype="f32", hubs=16384, learned=True, targets=[0.95], batching=True),
 }
 
 
@@ -244,7 +245,7 @@ def generate(spec, synth):
     if g == "highdim_f32":
         return synth.highdim_f32(n=spec["n"], nq=spec["nq"])
     if g == "batch_f32":
-        return synth.batch_f32(n=spec["n"], nq=spec["nq"])
+        return synth.batch_f32(n=spec["n"], nq=spec["nq"], n_train=spec["n_train"])
     return synth.small_u8(n=spec["n"], nq=spec["nq"])
 
 
@@ -591,10 +592,12 @@ def precision_report(W, torch, ann, args, dev):
     return out
 
 
-def batch_report(W, torch, ann, args, dev):
-    """Mixed per-query k and L in one persistent launch over the whole stream
-    (QPS, recall@k_i), then per-batch latency over consecutive batches of
-    1,000 queries, by direct calls and through a CUDA-graph plan (p50/p99)."""
+def batch_report(W, torch, ann, args, dev, modes):
+    """Per entry mode: mixed per-query k and L in one persistent launch over
+    the whole stream (QPS including entry selection, recall@k_i), then
+    per-batch latency over consecutive batches of 1,000 queries, by direct
+    calls and through a CUDA-graph plan of entry selection + search
+    (p50/p99)."""
     kq = torch.from_numpy(W["w"]["k"]).to(dev)
     Lq = torch.from_numpy(W["w"]["L"]).to(dev)
     q = W["q"]
@@ -602,55 +605,71 @@ def batch_report(W, torch, ann, args, dev):
     ids = torch.empty((nq, 100), dtype=torch.int32, device=dev)
     dd = torch.empty((nq, 100), dtype=torch.float32, device=dev)
     st = torch.empty((nq, 2), dtype=torch.int32, device=dev)
+    ent = torch.empty(nq, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
-    p = ann.search_params(100, 512, W=1, d_k=kq, d_L=Lq)
-    best, _ = ann.ann_autotune(W["h"], q, nq, None, p, ids, dd, 2, stream)
-    best.d_k, best.d_L = p.d_k, p.d_L
-    ann.ann_search_batch(W["h"], q, nq, None, best, ids, dd, st, stream)
-    if ann.ann_sync_status(W["h"], stream) != ann.OK:
-        raise RuntimeError("batched search reported a device error")
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(3):
-        ann.ann_search_batch(W["h"], q, nq, None, best, ids, dd, None, stream)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    qps = nq * 3 / (e0.elapsed_time(e1) / 1e3)
-    I = ids.cpu().numpy()
+    entry_mode = {"medoid": ann.ENTRY_MEDOID, "learned": ann.ENTRY_LEARNED_NAV,
+                  "exhaustive": ann.ENTRY_LEARNED_EXHAUSTIVE}
     kk = W["w"]["k"]
-    hits = sum(len(np.intersect1d(I[i, :kk[i]], W["gt"][i, :kk[i]])) for i in range(nq))
-    rec = hits / float(kk.sum())
-    s = st.cpu().numpy()
-    # per-batch latency
-    B = 1000
-    lat, lat_plan = [], []
-    for b0 in range(0, nq, B):
-        sl = slice(b0, b0 + B)
-        pb = ann.search_params(100, 512, W=1, hash_bits=best.hash_bits, stage_rows=best.stage_rows,
-                               team=best.team, spill_bits=best.spill_bits, d_k=kq[sl], d_L=Lq[sl])
-        a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        ann.ann_search_batch(W["h"], q[sl], B, None, pb, ids[sl], dd[sl], None, stream)
-        c.record(stream)
-        c.synchronize()
-        lat.append(a.elapsed_time(c))
-    qb, kb, lb = q[:B].clone(), kq[:B].clone(), Lq[:B].clone()
-    ib = torch.empty((B, 100), dtype=torch.int32, device=dev)
-    db = torch.empty((B, 100), dtype=torch.float32, device=dev)
-    pp = ann.search_params(100, 512, W=1, hash_bits=best.hash_bits, stage_rows=best.stage_rows,
-                           team=best.team, spill_bits=best.spill_bits, d_k=kb, d_L=lb)
-    plan = ann.ann_plan_create(W["h"], qb, B, ann.ENTRY_MEDOID, 0, pp, None, ib, db)
-    try:
-        for _ in range(100):
+    out = {}
+    for mode in modes:
+        em = entry_mode[mode]
+
+        def select(qq, n, e):
+            if em == ann.ENTRY_MEDOID:
+                return None
+            ann.ann_select_entry(W["h"], qq, n, em, args.l_hub, e, None, stream)
+            return e
+
+        p = ann.search_params(100, 512, W=args.W, d_k=kq, d_L=Lq)
+        best, _ = ann.ann_autotune(W["h"], q, nq, select(q, nq, ent), p, ids, dd, 2, stream)
+        best.d_k, best.d_L = p.d_k, p.d_L
+        ann.ann_search_batch(W["h"], q, nq, select(q, nq, ent), best, ids, dd, st, stream)
+        if ann.ann_sync_status(W["h"], stream) != ann.OK:
+            raise RuntimeError("batched search reported a device error")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            ann.ann_search_batch(W["h"], q, nq, select(q, nq, ent), best, ids, dd, None, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        qps = nq * 3 / (e0.elapsed_time(e1) / 1e3)
+        I = ids.cpu().numpy()
+        hits = sum(len(np.intersect1d(I[i, :kk[i]], W["gt"][i, :kk[i]])) for i in range(nq))
+        rec = hits / float(kk.sum())
+        s = st.cpu().numpy()
+        # per-batch latency
+        B = 1000
+        lat, lat_plan = [], []
+        eb = torch.empty(B, dtype=torch.int32, device=dev)
+        for b0 in range(0, nq, B):
+            sl = slice(b0, b0 + B)
+            pb = ann.search_params(100, 512, W=args.W, hash_bits=best.hash_bits, stage_rows=best.stage_rows,
+                                   team=best.team, spill_bits=best.spill_bits, d_k=kq[sl], d_L=Lq[sl])
             a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            ann.ann_plan_launch(plan, stream)
+            ann.ann_search_batch(W["h"], q[sl], B, select(q[sl], B, eb), pb, ids[sl], dd[sl], None, stream)
             c.record(stream)
             c.synchronize()
-            lat_plan.append(a.elapsed_time(c))
-    finally:
-        ann.ann_plan_free(plan)
-    return {"qps_one_launch": qps, "recall_at_own_k": rec, "queries": nq,
+            lat.append(a.elapsed_time(c))
+        qb, kb, lb = q[:B].clone(), kq[:B].clone(), Lq[:B].clone()
+        ib = torch.empty((B, 100), dtype=torch.int32, device=dev)
+        db = torch.empty((B, 100), dtype=torch.float32, device=dev)
+        pp = ann.search_params(100, 512, W=args.W, hash_bits=best.hash_bits, stage_rows=best.stage_rows,
+                               team=best.team, spill_bits=best.spill_bits, d_k=kb, d_L=lb)
+        plan = ann.ann_plan_create(W["h"], qb, B, em, args.l_hub, pp, None if em == ann.ENTRY_MEDOID else eb,
+                                   ib, db)
+        try:
+            for _ in range(100):
+                a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                ann.ann_plan_launch(plan, stream)
+                c.record(stream)
+                c.synchronize()
+                lat_plan.append(a.elapsed_time(c))
+        finally:
+            ann.ann_plan_free(plan)
+        out[mode] = {
+            "qps_one_launch": qps, "recall_at_own_k": rec, "queries": nq,
             "evals_per_query": float(s[:, 0].mean()), "hops_per_query": float(s[:, 1].mean()),
             "tuned": {"hash_bits": best.hash_bits, "stage_rows": best.stage_rows, "team": best.team,
                       "spill_bits": best.spill_bits},
@@ -658,6 +677,7 @@ def batch_report(W, torch, ann, args, dev):
                                              "p99": float(np.percentile(lat, 99))},
             "plan_latency_ms": {"p50": float(np.percentile(lat_plan, 50)),
                                 "p99": float(np.percentile(lat_plan, 99))}}
+    return out
 
 
 def run_gpu(args):
@@ -704,7 +724,8 @@ def run_gpu(args):
     e2e = end_to_end(R["run"], torch, R["L"], max(10, args.steps // 4))
     e2e["value"] *= world
     prec = precision_report(W, torch, ann, args, dev) if spec.get("precision") else None
-    batching = batch_report(W, torch, ann, args, dev) if spec.get("batching") else None
+    batching = batch_report(W, torch, ann, args, dev, ["medoid"] + ([head] if head != "medoid" else [])) \
+        if spec.get("batching") else None
     peak, peak_kind = peaks()
     achieved = R["alg_bytes"] / (search_ms / 1e3) / 1e9
     mt = MEASURED_TRAFFIC.get(args.workload)

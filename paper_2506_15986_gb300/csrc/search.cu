@@ -35,7 +35,7 @@ namespace ann {
 
 namespace {
 
-constexpr int kSearchWarps = 1;  // warps (teams) per CTA
+constexpr int kMaxSearchWarps = 2;  // warps (teams) per CTA: 1 or 2, whichever fits more teams
 constexpr int kTimeoutIters = 1 << 22;
 constexpr int kSlots = ANN_MAX_STEP_CAND / 32;  // neighbour slots per lane in one step
 
@@ -252,23 +252,27 @@ __device__ __forceinline__ uint32_t group_distance(const uint8_t *row, const uin
         // two FP32 accumulators (even and odd coordinates) held as one packed
         // pair: each f32x2 operation rounds both halves exactly as the scalar
         // operations would, at half the instruction count
-        uint64_t acc = 0;  // (0.f, 0.f)
+        // four FP32 accumulators (coordinates 4c+0..3) held as two packed
+        // pairs: each f32x2 operation rounds both halves exactly as the scalar
+        // operations would, at half the instruction count, and the two pairs
+        // are independent dependency chains
+        uint64_t acc = 0, acc2 = 0;  // (0.f, 0.f)
         auto acc4 = [&](float x0, float x1, float x2, float x3, float4 y) {
             if constexpr (MT == ANN_L2)
                 asm("{\n\t.reg .b64 x, y, d;\n\t"
-                    "mov.b64 x, {%1, %2};\n\tmov.b64 y, {%5, %6};\n\t"
+                    "mov.b64 x, {%2, %3};\n\tmov.b64 y, {%6, %7};\n\t"
                     "sub.rn.f32x2 d, x, y;\n\tfma.rn.f32x2 %0, d, d, %0;\n\t"
-                    "mov.b64 x, {%3, %4};\n\tmov.b64 y, {%7, %8};\n\t"
-                    "sub.rn.f32x2 d, x, y;\n\tfma.rn.f32x2 %0, d, d, %0;\n\t}"
-                    : "+l"(acc)
+                    "mov.b64 x, {%4, %5};\n\tmov.b64 y, {%8, %9};\n\t"
+                    "sub.rn.f32x2 d, x, y;\n\tfma.rn.f32x2 %1, d, d, %1;\n\t}"
+                    : "+l"(acc), "+l"(acc2)
                     : "f"(x0), "f"(x1), "f"(x2), "f"(x3), "f"(y.x), "f"(y.y), "f"(y.z), "f"(y.w));
             else
                 asm("{\n\t.reg .b64 x, y;\n\t"
-                    "mov.b64 x, {%1, %2};\n\tmov.b64 y, {%5, %6};\n\t"
+                    "mov.b64 x, {%2, %3};\n\tmov.b64 y, {%6, %7};\n\t"
                     "fma.rn.f32x2 %0, x, y, %0;\n\t"
-                    "mov.b64 x, {%3, %4};\n\tmov.b64 y, {%7, %8};\n\t"
-                    "fma.rn.f32x2 %0, x, y, %0;\n\t}"
-                    : "+l"(acc)
+                    "mov.b64 x, {%4, %5};\n\tmov.b64 y, {%8, %9};\n\t"
+                    "fma.rn.f32x2 %1, x, y, %1;\n\t}"
+                    : "+l"(acc), "+l"(acc2)
                     : "f"(x0), "f"(x1), "f"(x2), "f"(x3), "f"(y.x), "f"(y.y), "f"(y.z), "f"(y.w));
         };
         if constexpr (DT == ANN_F32) {
@@ -297,7 +301,8 @@ __device__ __forceinline__ uint32_t group_distance(const uint8_t *row, const uin
                 acc4(f2.x, f2.y, f3.x, f3.y, q4[2 * c + 1]);
             }
         }
-        float s = __uint_as_float(static_cast<uint32_t>(acc)) + __uint_as_float(static_cast<uint32_t>(acc >> 32));
+        float s = (__uint_as_float(static_cast<uint32_t>(acc)) + __uint_as_float(static_cast<uint32_t>(acc >> 32))) +
+                  (__uint_as_float(static_cast<uint32_t>(acc2)) + __uint_as_float(static_cast<uint32_t>(acc2 >> 32)));
         for (int o = G >> 1; o > 0; o >>= 1)
             s += __shfl_xor_sync(kFull, s, o);
         if constexpr (MT == ANN_IP)
@@ -307,7 +312,7 @@ __device__ __forceinline__ uint32_t group_distance(const uint8_t *row, const uin
 }
 
 template <int DT, int MT>
-__global__ void __launch_bounds__(32 * kSearchWarps) beam_search_kernel(const SearchArgs a)
+__global__ void __launch_bounds__(32 * kMaxSearchWarps) beam_search_kernel(const SearchArgs a)
 {
     extern __shared__ __align__(128) uint8_t smem[];
     const int lane = threadIdx.x & 31;
@@ -321,7 +326,7 @@ __global__ void __launch_bounds__(32 * kSearchWarps) beam_search_kernel(const Se
     uint64_t *ptop = reinterpret_cast<uint64_t *>(my + a.off_ptop);  // W keys for the prediction
     uint64_t *cbuf = reinterpret_cast<uint64_t *>(my + a.off_cbuf);
     uint32_t *htab = reinterpret_cast<uint32_t *>(my + a.off_hash);
-    const int team = blockIdx.x * kSearchWarps + wid;
+    const int team = blockIdx.x * (blockDim.x >> 5) + wid;
     // two global spill tables per team: 2^spill_bits slots, then one four
     // times larger for the rare query that outgrows the first
     uint32_t *gtab1 = a.spill + static_cast<size_t>(team) * (static_cast<size_t>(5) << a.spill_bits);
@@ -766,29 +771,45 @@ __global__ void __launch_bounds__(32 * kRerankWarps)
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+// Resident teams for `per_warp` bytes of shared memory per team, with one or
+// two teams per CTA, whichever fits more (each CTA also costs the SM a fixed
+// reserve of shared memory, which two teams share).
 template <int DT, int MT>
-ann_status teams_for(ann_index *idx, size_t smem, int *teams)
+ann_status teams_for(ann_index *idx, size_t per_warp, int *teams, int *wpc)
 {
     auto kern = beam_search_kernel<DT, MT>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
-    if (e != cudaSuccess)
-        return cuda_status(e);
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * kSearchWarps, smem);
-    if (e != cudaSuccess)
-        return cuda_status(e);
-    if (per_sm < 1)
+    int best = 0, best_w = 1;
+    for (int w = 1; w <= kMaxSearchWarps; ++w) {
+        const size_t smem = per_warp * w;
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) !=
+            cudaSuccess) {
+            cudaGetLastError();  // too large for one CTA: not a candidate
+            continue;
+        }
+        int per_sm = 0;
+        const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * w, smem);
+        if (e != cudaSuccess)
+            return cuda_status(e);
+        if (per_sm * w > best) {
+            best = per_sm * w;
+            best_w = w;
+        }
+    }
+    if (best < 1)
         return ANN_ERR_UNSUPPORTED;  // the per-query state does not fit in shared memory
-    *teams = per_sm * idx->num_sms * kSearchWarps;
+    const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               static_cast<int>(per_warp * best_w));
+    if (e != cudaSuccess)
+        return cuda_status(e);
+    *teams = best * idx->num_sms;
+    *wpc = best_w;
     return ANN_OK;
 }
 
 template <int DT, int MT>
-ann_status launch_typed(const SearchArgs &a, size_t smem, int teams, cudaStream_t s)
+ann_status launch_typed(const SearchArgs &a, size_t smem, int teams, int wpc, cudaStream_t s)
 {
-    const int grid = (teams + kSearchWarps - 1) / kSearchWarps;
-    beam_search_kernel<DT, MT><<<grid, 32 * kSearchWarps, smem, s>>>(a);
+    beam_search_kernel<DT, MT><<<teams / wpc, 32 * wpc, smem, s>>>(a);
     return cuda_status(cudaGetLastError());
 }
 
@@ -918,12 +939,11 @@ ann_status launch_search(ann_index *idx, const SearchLaunch &L, cudaStream_t s)
     a.off_hash = static_cast<int>(off);
     off = align_up(off + (hb > 0 ? static_cast<size_t>(4) << hb : 0), 128);
     a.per_warp = static_cast<int>(off);
-    const size_t smem = off * kSearchWarps;
 
     // persistent grid: occupancy-limited, at most one team per query
-    int teams = 0;
+    int teams = 0, wpc = 1;
     ann_status st = ANN_OK;
-    ANN_DISPATCH(teams_for, idx, smem, &teams);
+    ANN_DISPATCH(teams_for, idx, off, &teams, &wpc);
     if (st != ANN_OK)
         return st;
     if (L.max_teams > 0)
@@ -931,7 +951,8 @@ ann_status launch_search(ann_index *idx, const SearchLaunch &L, cudaStream_t s)
     teams = static_cast<int>(std::min<long long>(teams, L.nq));
     if (teams < 1)
         return ANN_OK;
-    teams = (teams + kSearchWarps - 1) / kSearchWarps * kSearchWarps;  // whole CTAs
+    teams = (teams + wpc - 1) / wpc * wpc;  // whole CTAs
+    const size_t smem = off * wpc;
 
     // scratch: work counter, then two spill tables per team
     const size_t need = search_scratch_bytes(teams, a.spill_bits);
@@ -960,7 +981,7 @@ ann_status launch_search(ann_index *idx, const SearchLaunch &L, cudaStream_t s)
     }
     cudaError_t e = cudaMemsetAsync(scratch, 0, 8, s);
     if (e == cudaSuccess) {
-        ANN_DISPATCH(launch_typed, a, smem, teams, s);
+        ANN_DISPATCH(launch_typed, a, smem, teams, wpc, s);
     } else {
         st = cuda_status(e);
     }

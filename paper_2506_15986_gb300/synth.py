@@ -160,11 +160,12 @@ def ip_f32(n=1_000_000, nq=10_000, n_train=0, d=200, n_comp=2000, noise=0.5, spe
     return dict(base=base, queries=q, train=train)
 
 
-def batch_f32(n=10_000_000, nq=100_000, d=96, n_comp=10_000, centre_scale=1.0, spectrum=0.5,
+def batch_f32(n=10_000_000, nq=100_000, n_train=0, d=96, n_comp=10_000, centre_scale=1.0, spectrum=0.5,
               seed=SEED_BASE + 5):
     """The shifted-mixture law of shift_f32 at d = 96 with 10,000 components;
     half of the query stream shifted; per-query k in {1, 10, 100} and L
-    uniform in [max(32, k), 512]."""
+    uniform in [max(32, k), 512]; training queries from the same law as the
+    stream (half shifted), drawn after everything else."""
     rng = _rng(seed)
     g = _spectrum(d, spectrum)
     centres = (rng.normal(0.0, centre_scale, size=(n_comp, d)) * g).astype(np.float32)
@@ -181,7 +182,13 @@ def batch_f32(n=10_000_000, nq=100_000, d=96, n_comp=10_000, centre_scale=1.0, s
     k = rng.choice(np.array([1, 10, 100], np.int32), size=nq)
     lo = np.maximum(32, k)
     L = (lo + np.floor(rng.random(nq) * (513 - lo))).astype(np.int32)
-    return dict(base=base, queries=q.astype(np.float32), k=k.astype(np.int32), L=L)
+    train = np.empty((0, d), np.float32)
+    if n_train:
+        tc = rng.integers(0, n_comp, size=n_train)
+        train = centres[tc] + scales[tc] * rng.standard_normal((n_train, d), dtype=np.float32)
+        train[n_train // 2:] += shifts[tc[n_train // 2:]]
+        train = train.astype(np.float32)
+    return dict(base=base, queries=q.astype(np.float32), k=k.astype(np.int32), L=L, train=train)
 
 
 def kmeans_init(m, k, seed):

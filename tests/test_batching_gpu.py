@@ -61,7 +61,7 @@ def _model(case):
     ann.ann_set_entry_model(case["h"], 128, W1, b1, W2, b2, hub_nodes, E, 8)
 
 
-@pytest.mark.parametrize("mode", [ann.ENTRY_MEDOID, ann.ENTRY_LEARNED_NAV])
+@pytest.mark.parametrize("mode", [ann.ENTRY_MEDOID, ann.ENTRY_LEARNED_NAV, ann.ENTRY_LEARNED_EXHAUSTIVE])
 def test_graph_plan_replays_the_batch(case, mode):
     if mode != ann.ENTRY_MEDOID:
         _model(case)
