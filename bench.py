@@ -53,7 +53,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "QPS at recall@10=0.95 on 1 GB300, learned vs medoid entry; dist evals/query"
 L_SWEEP = [16, 24, 32, 40, 48, 56, 64, 72, 80, 88, 96, 112, 128, 144, 160, 176, 192, 224, 256, 320,
-           384, 448, 512]
+           384, 448, 512, 640, 768, 1024, 1536, 2048]
 K_NN = 10
 
 WORKLOADS = {

@@ -61,7 +61,7 @@ typedef struct ann_index ann_index;
 #define ANN_SEARCH_RERANK 1u /* re-score the final pool from the fp32 copy (see ann_index_desc.base_f32) */
 
 /* Limits of one search */
-#define ANN_MAX_L 512      /* pool size L */
+#define ANN_MAX_L 2048     /* pool size L */
 #define ANN_MAX_W 4        /* entries expanded per step */
 #define ANN_MAX_STEP_CAND 128 /* W * degree */
 
@@ -322,7 +322,7 @@ ann_status ann_get_entry_model(const ann_index *idx, float *W1, float *b1, float
  *   d_queries  nq*dim rows as for ann_search_batch (16-byte aligned)
  *   mode       ann_entry_mode; the learned modes need an attached model
  *              (ANN_ERR_UNSUPPORTED otherwise)
- *   L_hub      pool size of the hub-graph search (ANN_ENTRY_LEARNED_NAV), 1..512
+ *   L_hub      pool size of the hub-graph search (ANN_ENTRY_LEARNED_NAV), 1..ANN_MAX_L
  *   d_entry    out: nq int32 node ids, ready for ann_search_batch
  *   d_qhat     out (optional): nq*64 fp32 normalised query embeddings
  * Asynchronous on `stream`; the query tower and the exhaustive hub scores run

@@ -20,7 +20,7 @@ OK, ERR_INVALID_ARG, ERR_IO, ERR_FORMAT, ERR_OOM, ERR_CUDA, ERR_CAPACITY, ERR_TI
 U8, F32, F16, BF16, I8S = 0, 1, 2, 3, 4
 L2, IP = 0, 1
 SEARCH_RERANK = 1
-MAX_L, MAX_W, MAX_STEP_CAND = 512, 4, 128
+MAX_L, MAX_W, MAX_STEP_CAND = 2048, 4, 128
 
 _c = ctypes
 _p = ctypes.c_void_p
