@@ -27,7 +27,8 @@ namespace ann {
 namespace {
 
 // 16 MiB per device: 64 BF16 embedding values, a hub index and a score per
-// query, i.e. 136 bytes, so at most 123,361 queries per call.
+// query, i.e. 136 bytes; with room left for aligning the three regions to
+// 256 bytes, at most 123,357 queries per call.
 constexpr size_t kNoAllocScratchBytes = static_cast<size_t>(16) << 20;
 constexpr size_t kNoAllocBytesPerQuery = 64 * 2 + 4 + 4;
 constexpr int64_t kNoAllocMaxQueries = static_cast<int64_t>(kNoAllocScratchBytes / kNoAllocBytesPerQuery) - 4;
