@@ -13,8 +13,10 @@ One step = one batch of the evaluation queries through the public path:
 ann_select_entry (query tower, then the hub-graph search or the exhaustive
 tensor-core hub scoring, whichever is faster) then ann_search_batch (W = 4
 pool entries expanded per step, fewer when W * R would pass 128 candidates;
-visited-table, gather and distance-team sizes picked by ann_autotune), at the pool size L* that first reaches
-recall@10 >= 0.95 in the L sweep.  `value` is the learned-entry QPS; the
+visited-table, gather and distance-team sizes picked by ann_autotune), at the
+smallest pool size L* found to reach recall@10 >= 0.95 (an L sweep, then a
+bisection between the last L below and the first L reaching the target).
+`value` is the learned-entry QPS; the
 medoid-entry numbers (same W, own L* and tuning) sit beside it in `config`.
 Inputs are resident in HBM when the timed region starts; every base set is
 larger than L2 (129 MB) except the small uint8 one, so no flush is needed.
@@ -164,6 +166,26 @@ def parse():
 def dist_env():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
             int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def max_over_ranks(x, world, device="cpu"):
+    """The largest x over all ranks of the default process group (x itself on
+    one rank).  device: where the reduction tensor lives (cuda for NCCL, cpu
+    for gloo)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as distd
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    distd.all_reduce(t, op=distd.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_qps(queries_per_rank, steps, world, slowest_ms):
+    """Whole-job throughput of query-parallel replicas: every rank searched
+    queries_per_rank queries per step, and the job took as long as its
+    slowest rank."""
+    return world * queries_per_rank * steps / (slowest_ms / 1e3)
 
 
 class Clocks:
@@ -395,14 +417,11 @@ class Runner:
 
 
 def sweep(run, torch, ann, W, targets):
-    """recall@k, evals, QPS per L (until the highest target is reached twice);
-    per target: the smallest swept L reaching it and the QPS interpolated at
-    exactly the target between the bracketing L."""
-    out = []
-    top = max(targets)
-    for L in L_SWEEP:
-        if L < run.k:
-            continue
+    """recall@k, evals, QPS per L (until the highest target is reached twice),
+    then a bisection between the last swept L below the main target and the
+    first one reaching it; per target: the smallest measured L reaching it and
+    the QPS interpolated at exactly the target between the bracketing L."""
+    def measure(L):
         run.step(L, stats=True)
         st = ann.ann_sync_status(run.h, run.stream)
         if st != ann.OK:
@@ -415,10 +434,31 @@ def sweep(run, torch, ann, W, targets):
             run.step(L)
         e1.record(run.stream)
         torch.cuda.synchronize()
-        out.append(dict(L=L, recall=r, evals=float(s[:, 0].mean()), hops=float(s[:, 1].mean()),
-                        qps=run.nq * 5 / (e0.elapsed_time(e1) / 1e3)))
+        return dict(L=L, recall=r, evals=float(s[:, 0].mean()), hops=float(s[:, 1].mean()),
+                    qps=run.nq * 5 / (e0.elapsed_time(e1) / 1e3))
+
+    out = []
+    top = max(targets)
+    for L in L_SWEEP:
+        if L < run.k:
+            continue
+        out.append(measure(L))
         if len([x for x in out if x["recall"] >= top]) >= 2:
             break
+    main = targets[0] if len(targets) == 1 else 0.95
+    first = next((i for i, x in enumerate(out) if x["recall"] >= main), None)
+    if first:
+        lo, hi = out[first - 1]["L"], out[first]["L"]
+        for _ in range(4):
+            if hi - lo <= 1:
+                break
+            x = measure((lo + hi) // 2)
+            out.append(x)
+            if x["recall"] >= main:
+                hi = x["L"]
+            else:
+                lo = x["L"]
+        out.sort(key=lambda x: x["L"])
     per = {}
     for t in targets:
         hit = [x for x in out if x["recall"] >= t]
@@ -429,8 +469,8 @@ def sweep(run, torch, ann, W, targets):
             if a["recall"] < t <= b["recall"]:
                 f = (t - a["recall"]) / (b["recall"] - a["recall"])
                 interp = a["qps"] + f * (b["qps"] - a["qps"])
+                break
         per[t] = dict(L=hit[0]["L"] if hit else None, qps_interp=interp)
-    main = targets[0] if len(targets) == 1 else 0.95
     Lstar = per[main]["L"] or out[-1]["L"]
     return Lstar, out, per
 
@@ -465,19 +505,15 @@ def timed(run, torch, ann, args, L, world, dev, nvtx=None):
     if world > 1:
         import torch.distributed as distd
         distd.barrier()
-    total_ms = t0.elapsed_time(t1)
+    total_ms = max_over_ranks(t0.elapsed_time(t1), world, dev)
     search_ms = float(np.mean([ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(args.steps)]))
-    if world > 1:
-        import torch.distributed as distd
-        tt = torch.tensor([total_ms], device=dev)
-        distd.all_reduce(tt, op=distd.ReduceOp.MAX)
-        total_ms = float(tt.item())
     return total_ms, search_ms, clk.summary()
 
 
-def end_to_end(run, torch, L, steps):
+def end_to_end(run, torch, L, steps, world=1, dev="cpu"):
     """Same metric through the public calls with host buffers: pinned H2D of the
-    queries, entry selection + search, D2H of ids and distances, every step."""
+    queries, entry selection + search, D2H of ids and distances, every step;
+    whole-job throughput over the ranks (slowest rank's time)."""
     W = run.W
     qh = torch.from_numpy(W["w"]["queries"]).pin_memory()
     ih = torch.empty(tuple(run.ids.shape), dtype=run.ids.dtype).pin_memory()
@@ -492,8 +528,8 @@ def end_to_end(run, torch, L, steps):
         ih.copy_(run.ids, non_blocking=True)
         dh.copy_(run.dists, non_blocking=True)
         run.stream.synchronize()
-    dt = time.perf_counter() - a0
-    return {"value": run.nq * steps / dt, "unit": "queries/s",
+    dt_ms = max_over_ranks(1e3 * (time.perf_counter() - a0), world, dev)
+    return {"value": job_qps(run.nq, steps, world, dt_ms), "unit": "queries/s",
             "h2d_bytes_per_step": int(qh.numel() * qh.element_size()),
             "d2h_bytes_per_step": int(ih.numel() * 4 + dh.numel() * 4)}
 
@@ -711,7 +747,7 @@ def run_gpu(args):
     head = max(learned_modes, key=lambda m: probe[m]) if learned_modes else "medoid"
     R = res[head]
     total_ms, search_ms, clocks = timed(R["run"], torch, ann, args, R["L"], world, dev, nvtx="headline")
-    value = world * R["run"].nq * args.steps / (total_ms / 1e3)
+    value = job_qps(R["run"].nq, args.steps, world, total_ms)
     others = {}
     for mode, r in res.items():
         if mode != head:
@@ -721,8 +757,7 @@ def run_gpu(args):
                                 hops_per_query=r["hops"],
                                 per_target={str(t): v for t, v in r["per_target"].items()},
                                 search_ms=sm, tuned=r["tune"], sweep=r["sweep"])
-    e2e = end_to_end(R["run"], torch, R["L"], max(10, args.steps // 4))
-    e2e["value"] *= world
+    e2e = end_to_end(R["run"], torch, R["L"], max(10, args.steps // 4), world, dev)
     prec = precision_report(W, torch, ann, args, dev) if spec.get("precision") else None
     batching = batch_report(W, torch, ann, args, dev, ["medoid"] + ([head] if head != "medoid" else [])) \
         if spec.get("batching") else None
