@@ -363,6 +363,16 @@ def build_learned(W, args, torch, ann, synth, dev):
                 epochs=args.epochs, lr=args.lr, tau=args.tau, batch=batch, times=times)
 
 
+def mode_info(ann, mode):
+    """(entry mode, seeds per query) of a bench mode name: medoid, learned
+    (hub-graph search), exhaustive (all hub scores), exhaustive_s<m> (the m
+    best hubs as a seed set)."""
+    base, _, seeds = mode.partition("_s")
+    em = {"medoid": ann.ENTRY_MEDOID, "learned": ann.ENTRY_LEARNED_NAV,
+          "exhaustive": ann.ENTRY_LEARNED_EXHAUSTIVE}[base]
+    return em, int(seeds) if seeds else 1
+
+
 class Runner:
     """One step = entry selection (learned modes) + batched search."""
 
@@ -378,11 +388,13 @@ class Runner:
         dd = torch.int32 if W["dt"] == ann.U8 else torch.float32
         self.dists = torch.empty((nq, k), dtype=dd, device=dev)
         self.stats = torch.empty((nq, 2), dtype=torch.int32, device=dev)
-        self.entry = torch.empty(nq, dtype=torch.int32, device=dev)
+        self.emode, self.seeds = mode_info(ann, mode)
+        self.entry = torch.empty((nq, self.seeds) if self.seeds > 1 else nq, dtype=torch.int32, device=dev)
         self.tuned = {}  # L -> ann_search_params picked by ann_autotune
 
     def params(self, L):
-        return self.tuned.get(L) or self.ann.search_params(self.k, L, W=self.args.W, flags=self.flags)
+        return self.tuned.get(L) or self.ann.search_params(
+            self.k, L, W=self.args.W, flags=self.flags, n_entries=self.seeds if self.seeds > 1 else 0)
 
     def autotune(self, L):
         """Pick the visited-table size and gather round size (speed-only knobs)."""
@@ -396,11 +408,14 @@ class Runner:
                 "search_ms": ms}
 
     def select(self, q):
-        if self.mode == "medoid":
+        if self.emode == self.ann.ENTRY_MEDOID:
             return None
-        m = self.ann.ENTRY_LEARNED_NAV if self.mode == "learned" else self.ann.ENTRY_LEARNED_EXHAUSTIVE
-        self.ann.ann_select_entry(self.h, q, self.nq, m, self.args.l_hub, self.entry, None,
-                                  self.stream)
+        if self.seeds > 1:
+            self.ann.ann_select_entries(self.h, q, self.nq, self.emode, self.args.l_hub, self.seeds,
+                                        self.entry, None, self.stream)
+        else:
+            self.ann.ann_select_entry(self.h, q, self.nq, self.emode, self.args.l_hub, self.entry, None,
+                                      self.stream)
         return self.entry
 
     def search(self, q, entry, L, stats=False):
@@ -413,7 +428,8 @@ class Runner:
 
     def launches(self):
         extra = 1 if self.flags else 0
-        return {"medoid": 1, "learned": 4, "exhaustive": 3}[self.mode] + extra
+        return {self.ann.ENTRY_MEDOID: 1, self.ann.ENTRY_LEARNED_NAV: 4,
+                self.ann.ENTRY_LEARNED_EXHAUSTIVE: 3}[self.emode] + extra
 
 
 def sweep(run, torch, ann, W, targets):
@@ -641,22 +657,22 @@ def batch_report(W, torch, ann, args, dev, modes):
     ids = torch.empty((nq, 100), dtype=torch.int32, device=dev)
     dd = torch.empty((nq, 100), dtype=torch.float32, device=dev)
     st = torch.empty((nq, 2), dtype=torch.int32, device=dev)
-    ent = torch.empty(nq, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
-    entry_mode = {"medoid": ann.ENTRY_MEDOID, "learned": ann.ENTRY_LEARNED_NAV,
-                  "exhaustive": ann.ENTRY_LEARNED_EXHAUSTIVE}
     kk = W["w"]["k"]
     out = {}
     for mode in modes:
-        em = entry_mode[mode]
+        em, seeds = mode_info(ann, mode)
+        ns = seeds if seeds > 1 else 0
+        shape = (lambda n: (n, seeds)) if seeds > 1 else (lambda n: (n,))
+        ent = torch.empty(shape(nq), dtype=torch.int32, device=dev)
 
         def select(qq, n, e):
             if em == ann.ENTRY_MEDOID:
                 return None
-            ann.ann_select_entry(W["h"], qq, n, em, args.l_hub, e, None, stream)
+            ann.ann_select_entries(W["h"], qq, n, em, args.l_hub, seeds, e, None, stream)
             return e
 
-        p = ann.search_params(100, 512, W=args.W, d_k=kq, d_L=Lq)
+        p = ann.search_params(100, 512, W=args.W, d_k=kq, d_L=Lq, n_entries=ns)
         best, _ = ann.ann_autotune(W["h"], q, nq, select(q, nq, ent), p, ids, dd, 2, stream)
         best.d_k, best.d_L = p.d_k, p.d_L
         ann.ann_search_batch(W["h"], q, nq, select(q, nq, ent), best, ids, dd, st, stream)
@@ -676,11 +692,12 @@ def batch_report(W, torch, ann, args, dev, modes):
         # per-batch latency
         B = 1000
         lat, lat_plan = [], []
-        eb = torch.empty(B, dtype=torch.int32, device=dev)
+        eb = torch.empty(shape(B), dtype=torch.int32, device=dev)
         for b0 in range(0, nq, B):
             sl = slice(b0, b0 + B)
             pb = ann.search_params(100, 512, W=args.W, hash_bits=best.hash_bits, stage_rows=best.stage_rows,
-                                   team=best.team, spill_bits=best.spill_bits, d_k=kq[sl], d_L=Lq[sl])
+                                   team=best.team, spill_bits=best.spill_bits, d_k=kq[sl], d_L=Lq[sl],
+                                   n_entries=ns)
             a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
             ann.ann_search_batch(W["h"], q[sl], B, select(q[sl], B, eb), pb, ids[sl], dd[sl], None, stream)
@@ -691,7 +708,7 @@ def batch_report(W, torch, ann, args, dev, modes):
         ib = torch.empty((B, 100), dtype=torch.int32, device=dev)
         db = torch.empty((B, 100), dtype=torch.float32, device=dev)
         pp = ann.search_params(100, 512, W=args.W, hash_bits=best.hash_bits, stage_rows=best.stage_rows,
-                               team=best.team, spill_bits=best.spill_bits, d_k=kb, d_L=lb)
+                               team=best.team, spill_bits=best.spill_bits, d_k=kb, d_L=lb, n_entries=ns)
         plan = ann.ann_plan_create(W["h"], qb, B, em, args.l_hub, pp, None if em == ann.ENTRY_MEDOID else eb,
                                    ib, db)
         try:
@@ -734,7 +751,8 @@ def run_gpu(args):
     targets = spec["targets"]
 
     res = {}
-    for mode in (["medoid", "learned", "exhaustive"] if spec["learned"] else ["medoid"]):
+    for mode in (["medoid", "learned", "exhaustive", "exhaustive_s2", "exhaustive_s4"] if spec["learned"]
+                 else ["medoid"]):
         res[mode] = measure_mode(Runner(W, torch, ann, args, mode), torch, ann, W, args, targets)
     # a short timing of every mode picks the headline: the faster learned mode
     # (hub-graph search or exhaustive tensor-core hub scoring), medoid without

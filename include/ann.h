@@ -59,11 +59,13 @@ typedef struct ann_index ann_index;
 
 /* Search flags */
 #define ANN_SEARCH_RERANK 1u /* re-score the final pool from the fp32 copy (see ann_index_desc.base_f32) */
+#define ANN_SEARCH_FAULT_WAIT 2u /* fault injection for tests of the timeout path (see ann_search_params) */
 
 /* Limits of one search */
 #define ANN_MAX_L 2048     /* pool size L */
 #define ANN_MAX_W 4        /* entries expanded per step */
 #define ANN_MAX_STEP_CAND 128 /* W * degree */
+#define ANN_MAX_SEEDS 32   /* seed nodes per query (n_entries) */
 
 /*
  * Index description for ann_index_create.  The path searches a fixed-degree
@@ -115,6 +117,11 @@ typedef struct {
  *             1, 2, 4, 8, 16 or 32.  Speed only for uint8 data; for float
  *             data it sets the FP32 summation order, so distances may differ
  *             in the last bits between teams
+ *   n_entries seeds per query in d_entry (0 or 1: one), 1..ANN_MAX_SEEDS:
+ *             d_entry is then nq x n_entries node ids, -1 marking an unused
+ *             slot (at least one per query).  The initial pool holds every
+ *             distinct seed, each evaluated once (Algorithm 1 starts from a
+ *             set of nodes; one seed is the NSG-style single entry)
  *   spill_bits log2 of the slots of the first global visited table a query
  *             moves to when its shared table fills (the second one has four
  *             times as many), 0 = chosen from L; 10..16.  Speed only, unless
@@ -124,7 +131,12 @@ typedef struct {
  *             index's fp32 copy of the rows (ann_index_desc.base_f32; without
  *             it the call returns ANN_ERR_UNSUPPORTED) and the k best by
  *             (fp32 distance, id) are returned (the precision line: reduced-
- *             precision storage for traversal, exact scores for the answer)
+ *             precision storage for traversal, exact scores for the answer).
+ *             ANN_SEARCH_FAULT_WAIT: fault injection for testing; every wait
+ *             for a round of gathered rows gives up at once, as if its time
+ *             limit had passed: each query fails with -1 ids and the call
+ *             reports ANN_ERR_TIMEOUT through ann_sync_status.  The copies in
+ *             flight still land, so the device and the index stay usable.
  *   d_k, d_L  optional per-query k and L (device int32[nq]); NULL = k, L
  *   d_target  optional per-query target node (device int32[nq]); when given
  *             the search runs in label mode: it stops after the step in which
@@ -139,6 +151,7 @@ typedef struct {
     int32_t stage_rows;
     int32_t team;
     int32_t spill_bits;
+    int32_t n_entries;
     uint32_t flags;
     const int32_t *d_k;
     const int32_t *d_L;
@@ -201,7 +214,8 @@ ann_status ann_load_index(const char *path, int device, ann_index **out);
  * unvisited neighbour once, and stop when the pool holds no unexpanded entry.
  *   d_queries nq*dim query rows: uint8 for an ANN_U8 index, fp32 otherwise
  *   nq        number of queries (0 is accepted and queues nothing)
- *   d_entry   per-query entry node (device int32[nq]) or NULL for the medoid
+ *   d_entry   per-query entry node (device int32[nq]), or nq x p->n_entries
+ *             seed nodes when p->n_entries > 1, or NULL for the medoid
  *   p         search parameters (host pointer)
  *   d_ids     out: nq*k int32 node ids, best first; -1 pads missing results
  *   d_dists   out: nq*k distances, int32 for ANN_U8 and fp32 otherwise
@@ -229,8 +243,10 @@ typedef struct ann_plan ann_plan;
  * Capture one batch -- entry selection (entry_mode, L_hub as in
  * ann_select_entry; ANN_ENTRY_MEDOID skips it) followed by ann_search_batch
  * with parameters p -- into a CUDA graph over fixed buffers.  The plan keeps
- * the pointers: queries, per-query arrays of p, d_entry_buf (nq int32,
- * needed unless the mode is ANN_ENTRY_MEDOID) and the outputs must stay
+ * the pointers: queries, per-query arrays of p, d_entry_buf (nq x
+ * max(1, p->n_entries) int32, needed unless the mode is ANN_ENTRY_MEDOID;
+ * with p->n_entries > 1 the plan selects seed sets with ann_select_entries)
+ * and the outputs must stay
  * valid while the plan is used.  Blocking; the index must not be freed
  * before the plan.
  */
@@ -330,6 +346,22 @@ ann_status ann_get_entry_model(const ann_index *idx, float *W1, float *b1, float
  */
 ann_status ann_select_entry(ann_index *idx, const void *d_queries, int64_t nq, int32_t mode,
                             int32_t L_hub, int32_t *d_entry, float *d_qhat, void *stream);
+
+/*
+ * Seed sets per query: the m_seeds best hubs of each query, best first
+ * (Algorithm 1 starts from a set of nodes; Sec. 4.3 scores every hub for the
+ * query, so its top hubs are the natural seeds).  ANN_ENTRY_LEARNED_EXHAUSTIVE
+ * keeps the top m_seeds of all hub scores (ties to the smaller hub index);
+ * ANN_ENTRY_LEARNED_NAV takes the m_seeds best of the hub-graph search's pool
+ * (L_hub >= m_seeds); ANN_ENTRY_MEDOID gives the medoid and unused slots.
+ *   m_seeds    1..ANN_MAX_ENTRY_HUBS
+ *   d_entry    out: nq*m_seeds int32 node ids (-1 = unused slot), ready for
+ *              ann_search_batch with ann_search_params.n_entries = m_seeds
+ *   other arguments as for ann_select_entry, which is the m_seeds = 1 case.
+ */
+#define ANN_MAX_ENTRY_HUBS 4
+ann_status ann_select_entries(ann_index *idx, const void *d_queries, int64_t nq, int32_t mode, int32_t L_hub,
+                              int32_t m_seeds, int32_t *d_entry, float *d_qhat, void *stream);
 
 /*
  * Exhaustive learned entry selection (the ANN_ENTRY_LEARNED_EXHAUSTIVE mode

@@ -52,7 +52,7 @@ def _lib():
         p, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
         lib.or_knn.argtypes = [p, i64, i32, i32, i32, p, i64, i32, p, p, p, i32]
         lib.or_knn.restype = i32
-        lib.or_search.argtypes = [p, i64, i32, i32, i32, p, i32, p, i64, p, i32,
+        lib.or_search.argtypes = [p, i64, i32, i32, i32, p, i32, p, i64, p, i32, i32,
                                   i32, p, p, i32, i32, p, p, p, p, p, i32]
         lib.or_search.restype = i32
         lib.or_medoid.argtypes = [p, i64, i32, i32]
@@ -116,6 +116,9 @@ def search(base, graph, queries, entries, L, k, metric=L2, W=1, Ls=None,
            ks=None, targets=None, threads=None):
     """Greedy best-first graph search (Sec. 2.1, Algorithm 1), sorted-pool form.
 
+    entries: one node per query (scalar or [nq]) or a seed set per query
+    ([nq, m], -1 = unused slot, at least one node): the initial pool holds
+    every distinct seed, each evaluated once.
     Returns (ids [nq, kstride], dists float64, evals, hops); kstride = max k.
     With ``targets`` the search stops once the target id has been evaluated
     and reports the counters at that step (label mode, Sec. 4.2 Def. 4);
@@ -124,7 +127,9 @@ def search(base, graph, queries, entries, L, k, metric=L2, W=1, Ls=None,
     g = np.ascontiguousarray(graph, np.int32)
     q = np.ascontiguousarray(queries, dtype=np.float64)
     nq, d = q.shape
-    ent = np.ascontiguousarray(np.broadcast_to(np.asarray(entries, np.int32), (nq,)))
+    e = np.asarray(entries, np.int32)
+    m = e.shape[1] if e.ndim == 2 else 1
+    ent = np.ascontiguousarray(np.broadcast_to(e, (nq, m) if e.ndim == 2 else (nq,)))
     Ls_a = None if Ls is None else np.ascontiguousarray(Ls, np.int32)
     ks_a = None if ks is None else np.ascontiguousarray(ks, np.int32)
     kstride = int(ks_a.max()) if ks_a is not None and nq else int(k)
@@ -134,7 +139,7 @@ def search(base, graph, queries, entries, L, k, metric=L2, W=1, Ls=None,
     ev = np.empty(nq, np.int32)
     hp = np.empty(nq, np.int32)
     rc = _lib().or_search(_ptr(base), base.shape[0], d, dt, metric, _ptr(g),
-                          g.shape[1], _ptr(q), nq, _ptr(ent), int(L), int(k),
+                          g.shape[1], _ptr(q), nq, _ptr(ent), int(m), int(L), int(k),
                           _ptr(Ls_a), _ptr(ks_a), kstride, int(W), _ptr(tg),
                           _ptr(ids), _ptr(dists), _ptr(ev), _ptr(hp),
                           _threads(threads))

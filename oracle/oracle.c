@@ -208,7 +208,7 @@ static void pool_insert(or_pool *P, double d, int32_t id)
 
 static void or_search_one(const void *base, int64_t n, int d, int dtype,
                           int metric, const int32_t *graph, int R,
-                          const double *q, int32_t entry, int L, int k, int W,
+                          const double *q, const int32_t *seeds, int m, int L, int k, int W,
                           int32_t target, uint8_t *visited, int32_t *touched,
                           or_pool *P, int32_t *sel, int32_t *out_ids,
                           double *out_dists, int32_t *out_evals,
@@ -219,10 +219,17 @@ static void or_search_one(const void *base, int64_t n, int d, int dtype,
     int done_target = 0;
     P->cnt = 0;
     P->cap = L;
-    visited[entry] = 1;
-    touched[nt++] = entry;
-    pool_insert(P, delta_q(base, dtype, metric, entry, d, q), entry);
-    evals = 1;
+    /* the initial pool: every distinct seed (Algorithm 1 starts from a set of
+     * nodes; -1 marks an unused seed slot) */
+    for (int e = 0; e < m; ++e) {
+        const int32_t s = seeds[e];
+        if (s < 0 || visited[s])
+            continue;
+        visited[s] = 1;
+        touched[nt++] = s;
+        pool_insert(P, delta_q(base, dtype, metric, s, d, q), s);
+        evals++;
+    }
     if (target >= 0 && visited[target])
         done_target = 1;
     while (!done_target) {
@@ -266,25 +273,32 @@ static void or_search_one(const void *base, int64_t n, int d, int dtype,
 }
 
 /*
- * Batch driver.  Per query i: entry entries[i]; pool size Ls ? Ls[i] : L;
+ * Batch driver.  Per query i: seeds entries[i*m .. i*m+m) (-1 = unused, at
+ * least one node id); pool size Ls ? Ls[i] : L;
  * result size ks ? ks[i] : k (rows of out_ids/out_dists have stride kstride);
  * target targets ? targets[i] : -1.  Queries run in parallel, one per thread.
  */
 int or_search(const void *base, int64_t n, int d, int dtype, int metric,
               const int32_t *graph, int R, const double *queries, int64_t nq,
-              const int32_t *entries, int L, int k, const int32_t *Ls,
+              const int32_t *entries, int m, int L, int k, const int32_t *Ls,
               const int32_t *ks, int kstride, int W, const int32_t *targets,
               int32_t *out_ids, double *out_dists, int32_t *out_evals,
               int32_t *out_hops, int nthreads)
 {
     if (!base || !graph || !queries || !entries || !out_ids || !out_dists ||
         !out_evals || !out_hops || n <= 0 || d <= 0 || R <= 0 || W <= 0 ||
-        kstride <= 0)
+        kstride <= 0 || m <= 0)
         return OR_ERR_ARG;
     for (int64_t i = 0; i < nq; ++i) {
         int Li = Ls ? Ls[i] : L, ki = ks ? ks[i] : k;
-        if (entries[i] < 0 || entries[i] >= n || Li <= 0 || ki <= 0 || ki > Li ||
-            ki > kstride)
+        int valid = 0;
+        for (int e = 0; e < m; ++e) {
+            const int32_t s = entries[i * (int64_t)m + e];
+            if (s < -1 || s >= n)
+                return OR_ERR_ARG;
+            valid += s >= 0;
+        }
+        if (!valid || Li <= 0 || ki <= 0 || ki > Li || ki > kstride)
             return OR_ERR_ARG;
     }
     int err = 0;
@@ -313,7 +327,7 @@ int or_search(const void *base, int64_t n, int d, int dtype, int metric,
                 int32_t *oi = out_ids + i * (int64_t)kstride;
                 double *od = out_dists + i * (int64_t)kstride;
                 or_search_one(base, n, d, dtype, metric, graph, R,
-                              queries + i * (int64_t)d, entries[i], Li, ki, W,
+                              queries + i * (int64_t)d, entries + i * (int64_t)m, m, Li, ki, W,
                               targets ? targets[i] : -1, visited, touched, &P,
                               sel, oi, od, out_evals + i, out_hops + i);
                 for (int j = ki; j < kstride; ++j) {

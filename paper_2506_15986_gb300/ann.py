@@ -19,8 +19,8 @@ OK, ERR_INVALID_ARG, ERR_IO, ERR_FORMAT, ERR_OOM, ERR_CUDA, ERR_CAPACITY, ERR_TI
 # ann_dtype / ann_metric
 U8, F32, F16, BF16, I8S = 0, 1, 2, 3, 4
 L2, IP = 0, 1
-SEARCH_RERANK = 1
-MAX_L, MAX_W, MAX_STEP_CAND = 2048, 4, 128
+SEARCH_RERANK, SEARCH_FAULT_WAIT = 1, 2
+MAX_L, MAX_W, MAX_STEP_CAND, MAX_SEEDS, MAX_ENTRY_HUBS = 2048, 4, 128, 32, 4
 
 _c = ctypes
 _p = ctypes.c_void_p
@@ -35,7 +35,7 @@ class ann_index_desc(ctypes.Structure):
 class ann_search_params(ctypes.Structure):
     _fields_ = [("k", _c.c_int32), ("L", _c.c_int32), ("W", _c.c_int32),
                 ("hash_bits", _c.c_int32), ("stage_rows", _c.c_int32), ("team", _c.c_int32),
-                ("spill_bits", _c.c_int32),
+                ("spill_bits", _c.c_int32), ("n_entries", _c.c_int32),
                 ("flags", _c.c_uint32), ("d_k", _p),
                 ("d_L", _p), ("d_target", _p)]
 
@@ -88,6 +88,7 @@ def load_library(path: str | None = None):
         "ann_set_entry_model": ([_p, _c.POINTER(ann_entry_model_desc), _p], i32),
         "ann_get_entry_model": ([_p] + [_p] * 7 + [_c.POINTER(i32)], i32),
         "ann_select_entry": ([_p, _p, i64, i32, i32, _p, _p, _p], i32),
+        "ann_select_entries": ([_p, _p, i64, i32, i32, i32, _p, _p, _p], i32),
         "ann_trainer_create": ([i32, i32, i32, _p, _p, _p, _p, _p, i64, _c.c_float, _c.c_float,
                                 _c.c_float, _c.c_float, _c.c_float, pp], i32),
         "ann_trainer_free": ([_p], i32),
@@ -193,9 +194,10 @@ def ann_load_index(path, device=0):
 
 
 def search_params(k, L, W=1, hash_bits=0, flags=0, d_k=None, d_L=None, d_target=None,
-                  stage_rows=0, team=0, spill_bits=0):
+                  stage_rows=0, team=0, spill_bits=0, n_entries=0):
     return ann_search_params(k=int(k), L=int(L), W=int(W), hash_bits=int(hash_bits),
                              stage_rows=int(stage_rows), team=int(team), spill_bits=int(spill_bits),
+                             n_entries=int(n_entries),
                              flags=int(flags), d_k=_ptr(d_k), d_L=_ptr(d_L),
                              d_target=_ptr(d_target))
 
@@ -266,6 +268,15 @@ def ann_select_entry(h, queries, nq, mode, L_hub, entry_out, qhat_out=None, stre
     _check(load_library().ann_select_entry(h, _ptr(queries), int(nq), int(mode), int(L_hub),
                                            _ptr(entry_out), _ptr(qhat_out), _stream(stream)),
            "ann_select_entry")
+
+
+def ann_select_entries(h, queries, nq, mode, L_hub, m_seeds, entry_out, qhat_out=None, stream=None):
+    """Queue seed-set selection: the m_seeds best hubs' nodes per query land
+    in entry_out (device int32[nq, m_seeds], -1 = unused slot)."""
+    _check(load_library().ann_select_entries(h, _ptr(queries), int(nq), int(mode), int(L_hub),
+                                             int(m_seeds), _ptr(entry_out), _ptr(qhat_out),
+                                             _stream(stream)),
+           "ann_select_entries")
 
 
 def ann_trainer_create(in_dim, W1, b1, W2, b2, hub_emb, max_batch, tau=0.07, lr=5e-5,

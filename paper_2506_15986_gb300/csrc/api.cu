@@ -385,9 +385,10 @@ ann_status ann_search_batch(ann_index *idx, const void *d_queries, int64_t nq, c
         (p->hash_bits != 0 && p->hash_bits != -1 && (p->hash_bits < 8 || p->hash_bits > 15)) ||
         p->stage_rows < 0 ||
         p->stage_rows > 32 || p->team < 0 || p->team > 32 || (p->team & (p->team - 1)) != 0 ||
-        (p->spill_bits != 0 && (p->spill_bits < 10 || p->spill_bits > 16)))
+        (p->spill_bits != 0 && (p->spill_bits < 10 || p->spill_bits > 16)) || p->n_entries < 0 ||
+        p->n_entries > ANN_MAX_SEEDS || (p->n_entries > 1 && !d_entry))
         return ANN_ERR_INVALID_ARG;
-    if (p->flags & ~ANN_SEARCH_RERANK)
+    if (p->flags & ~(ANN_SEARCH_RERANK | ANN_SEARCH_FAULT_WAIT))
         return ANN_ERR_INVALID_ARG;
     if ((p->flags & ANN_SEARCH_RERANK) && !idx->d_base_f32)
         return ANN_ERR_UNSUPPORTED;  // the exact rerank needs the fp32 copy of the rows
@@ -404,6 +405,7 @@ ann_status ann_search_batch(ann_index *idx, const void *d_queries, int64_t nq, c
     L.qbytes = idx->dtype == ANN_U8 ? idx->dim : idx->dim * 4;
     L.nq = nq;
     L.entries = d_entry;
+    L.n_entries = p->n_entries;
     L.p = p;
     L.ids = d_ids;
     L.dists = d_dists;

@@ -185,6 +185,9 @@ __global__ void __launch_bounds__(128) tower_forward_kernel(const TowerArgs t)
 // 100 KB keeps at most two CTAs (2 x 256 TMEM columns) on an SM
 constexpr int kArgmaxSmem = 100 * 1024;
 
+// One thread per query row keeps the M best (score, hub) pairs, ties to the
+// smaller hub index; outputs are nq x M, best first (M = 1: the argmax).
+template <int M>
 __global__ void __launch_bounds__(128)
     hub_argmax_kernel(const Operand Q, const __nv_bfloat16 *Eb, int H, int64_t nq, const int32_t *hub_nodes,
                       int32_t *out_node, int32_t *out_hub, float *out_score, int *status)
@@ -210,8 +213,13 @@ __global__ void __launch_bounds__(128)
     const uint32_t my_lane = tmem + (static_cast<uint32_t>(warp * 32) << 16);
     uint32_t phase = 0;
     const Operand E{Eb, OP_BF16, 64, 1, H, 64, nullptr};
-    float best = -INFINITY;
-    int bi = -1;
+    float best[M];
+    int bi[M];
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+        best[j] = -INFINITY;
+        bi[j] = -1;
+    }
     bool ok = true;
     for (int c0 = 0; c0 < H && ok; c0 += 256) {
         ok = tc_gemm_tile<256>(Q, r0, E, c0, 64, sA, sB, bar, phase, tmem);
@@ -223,9 +231,20 @@ __global__ void __launch_bounds__(128)
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
                 const int col = c0 + cc + j;
-                if (col < H && v[j] > best) {  // strict: the first maximum wins
-                    best = v[j];
-                    bi = col;
+                if (col < H && v[j] > best[M - 1]) {  // strict: the first of equal scores wins
+                    float sv = v[j];
+                    int si = col;
+#pragma unroll
+                    for (int t = 0; t < M; ++t) {
+                        if (sv > best[t]) {
+                            const float tv = best[t];
+                            const int ti = bi[t];
+                            best[t] = sv;
+                            bi[t] = si;
+                            sv = tv;
+                            si = ti;
+                        }
+                    }
                 }
             }
         }
@@ -234,13 +253,16 @@ __global__ void __launch_bounds__(128)
     if (!ok && threadIdx.x == 0)
         atomicOr(status, kStatusTimeoutBit);
     if (row < nq) {
-        const bool good = ok && bi >= 0;
-        if (out_hub)
-            out_hub[row] = good ? bi : -1;
-        if (out_score)
-            out_score[row] = good ? best : -INFINITY;
-        if (out_node)
-            out_node[row] = good ? hub_nodes[bi] : -1;
+#pragma unroll
+        for (int j = 0; j < M; ++j) {
+            const bool good = ok && bi[j] >= 0;
+            if (out_hub)
+                out_hub[row * M + j] = good ? bi[j] : -1;
+            if (out_score)
+                out_score[row * M + j] = good ? best[j] : -INFINITY;
+            if (out_node)
+                out_node[row * M + j] = good ? hub_nodes[bi[j]] : -1;
+        }
     }
     tc_fence_before();
     __syncthreads();
@@ -328,21 +350,25 @@ __global__ void hub_entry_kernel(const float *E, int H, int32_t *out)
     }
 }
 
-__global__ void map_hub_nodes(const int32_t *hub_ids, int64_t nq, int stride, const int32_t *hub_nodes,
+// Seed sets from the hub-graph search: out[i*m + j] = node of the j-th hub
+// found for query i; a missing first hub falls back to the medoid, a missing
+// later one is an unused slot (-1).
+__global__ void map_hub_seeds(const int32_t *hub_ids, int64_t nq, int m, const int32_t *hub_nodes,
                               int32_t medoid, int32_t *out)
 {
     const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-    if (i < nq) {
-        const int32_t h = hub_ids[i * stride];
-        out[i] = h >= 0 ? hub_nodes[h] : medoid;
+    if (i < nq * m) {
+        const int32_t h = hub_ids[i];
+        out[i] = h >= 0 ? hub_nodes[h] : (i % m == 0 ? medoid : -1);
     }
 }
 
-__global__ void fill_i32(int32_t *p, int64_t n, int32_t v)
+// medoid seed sets: the medoid first, the other slots unused
+__global__ void fill_medoid_seeds(int32_t *out, int64_t nq, int m, int32_t medoid)
 {
     const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-    if (i < n)
-        p[i] = v;
+    if (i < nq * m)
+        out[i] = i % m == 0 ? medoid : -1;
 }
 
 template <typename T>
@@ -412,18 +438,31 @@ ann_status launch_tower(const ann_entry_model *m, const Operand &X, int64_t nq, 
     return cuda_status(cudaGetLastError());
 }
 
-ann_status launch_hub_argmax(const ann_entry_model *m, const Operand &Q, int64_t nq, int32_t *out_node,
-                             int32_t *out_hub, float *out_score, int *status, cudaStream_t s)
+template <int M>
+ann_status launch_hub_topm(const ann_entry_model *m, const Operand &Q, int64_t nq, int32_t *out_node,
+                           int32_t *out_hub, float *out_score, int *status, cudaStream_t s)
 {
-    if (nq == 0)
-        return ANN_OK;
-    cudaError_t e = cudaFuncSetAttribute(hub_argmax_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(hub_argmax_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          kArgmaxSmem);
     if (e != cudaSuccess)
         return cuda_status(e);
-    hub_argmax_kernel<<<static_cast<unsigned>((nq + 127) / 128), 128, kArgmaxSmem, s>>>(
+    hub_argmax_kernel<M><<<static_cast<unsigned>((nq + 127) / 128), 128, kArgmaxSmem, s>>>(
         Q, m->Eb, m->H, nq, m->hub_nodes, out_node, out_hub, out_score, status);
     return cuda_status(cudaGetLastError());
+}
+
+ann_status launch_hub_argmax(const ann_entry_model *m, const Operand &Q, int64_t nq, int32_t *out_node,
+                             int32_t *out_hub, float *out_score, int *status, cudaStream_t s, int topm)
+{
+    if (nq == 0)
+        return ANN_OK;
+    switch (topm) {
+    case 1: return launch_hub_topm<1>(m, Q, nq, out_node, out_hub, out_score, status, s);
+    case 2: return launch_hub_topm<2>(m, Q, nq, out_node, out_hub, out_score, status, s);
+    case 3: return launch_hub_topm<3>(m, Q, nq, out_node, out_hub, out_score, status, s);
+    case 4: return launch_hub_topm<4>(m, Q, nq, out_node, out_hub, out_score, status, s);
+    default: return ANN_ERR_INVALID_ARG;
+    }
 }
 
 ann_status build_hub_index(ann_index *idx, ann_entry_model *m, const int32_t *hub_graph, int32_t hub_entry,
@@ -590,8 +629,14 @@ ann_status ann_get_entry_model(const ann_index *idx, float *W1, float *b1, float
 ann_status ann_select_entry(ann_index *idx, const void *d_queries, int64_t nq, int32_t mode, int32_t L_hub,
                             int32_t *d_entry, float *d_qhat, void *stream)
 {
-    if (!idx || nq < 0 || (mode != ANN_ENTRY_MEDOID && mode != ANN_ENTRY_LEARNED_NAV &&
-                           mode != ANN_ENTRY_LEARNED_EXHAUSTIVE))
+    return ann_select_entries(idx, d_queries, nq, mode, L_hub, 1, d_entry, d_qhat, stream);
+}
+
+ann_status ann_select_entries(ann_index *idx, const void *d_queries, int64_t nq, int32_t mode, int32_t L_hub,
+                              int32_t m_seeds, int32_t *d_entry, float *d_qhat, void *stream)
+{
+    if (!idx || nq < 0 || m_seeds < 1 || m_seeds > ANN_MAX_ENTRY_HUBS ||
+        (mode != ANN_ENTRY_MEDOID && mode != ANN_ENTRY_LEARNED_NAV && mode != ANN_ENTRY_LEARNED_EXHAUSTIVE))
         return ANN_ERR_INVALID_ARG;
     if (nq == 0)
         return ANN_OK;
@@ -603,20 +648,22 @@ ann_status ann_select_entry(ann_index *idx, const void *d_queries, int64_t nq, i
     cudaGetDevice(&prev);
     cudaSetDevice(idx->device);
     ann_status st = ANN_OK;
+    const int64_t nm = nq * m_seeds;
     if (mode == ANN_ENTRY_MEDOID) {
-        fill_i32<<<static_cast<unsigned>((nq + 255) / 256), 256, 0, s>>>(d_entry, nq, idx->medoid);
+        fill_medoid_seeds<<<static_cast<unsigned>((nm + 255) / 256), 256, 0, s>>>(d_entry, nq, m_seeds,
+                                                                                  idx->medoid);
         st = cuda_status(cudaGetLastError());
         cudaSetDevice(prev);
         return st;
     }
     ann_entry_model *m = idx->model;
-    if (!m || (mode == ANN_ENTRY_LEARNED_NAV && (L_hub < 1 || L_hub > ANN_MAX_L))) {
+    if (!m || (mode == ANN_ENTRY_LEARNED_NAV && (L_hub < m_seeds || L_hub > ANN_MAX_L))) {
         cudaSetDevice(prev);
         return m ? ANN_ERR_INVALID_ARG : ANN_ERR_UNSUPPORTED;
     }
     // scratch: q_hat fp32 + bf16, hub ids, hub scores
     const size_t qf = static_cast<size_t>(nq) * 64 * 4, qb = static_cast<size_t>(nq) * 64 * 2;
-    const size_t hb = static_cast<size_t>(nq) * 4;
+    const size_t hb = static_cast<size_t>(nm) * 4;
     void *scr = nullptr;
     st = scratch_alloc(idx, qf + qb + 2 * hb + 256, s, &scr);
     if (st != ANN_OK) {
@@ -631,10 +678,10 @@ ann_status ann_select_entry(ann_index *idx, const void *d_queries, int64_t nq, i
     st = launch_tower(m, X, nq, qhat, qbf, nullptr, nullptr, nullptr, idx->d_status, s);
     if (st == ANN_OK && mode == ANN_ENTRY_LEARNED_EXHAUSTIVE) {
         const Operand Q{qbf, OP_BF16, 64, 1, nq, 64, nullptr};
-        st = launch_hub_argmax(m, Q, nq, d_entry, hid, hsc, idx->d_status, s);
+        st = launch_hub_argmax(m, Q, nq, d_entry, hid, hsc, idx->d_status, s, m_seeds);
     } else if (st == ANN_OK) {
         ann_search_params p{};
-        p.k = 1;
+        p.k = m_seeds;
         p.L = L_hub;
         p.W = 1;
         SearchLaunch Ls{};
@@ -648,8 +695,8 @@ ann_status ann_select_entry(ann_index *idx, const void *d_queries, int64_t nq, i
         Ls.stats = nullptr;
         st = launch_search(m->hub_index, Ls, s);
         if (st == ANN_OK) {
-            map_hub_nodes<<<static_cast<unsigned>((nq + 255) / 256), 256, 0, s>>>(hid, nq, 1, m->hub_nodes,
-                                                                                  idx->medoid, d_entry);
+            map_hub_seeds<<<static_cast<unsigned>((nm + 255) / 256), 256, 0, s>>>(hid, nq, m_seeds, m->hub_nodes,
+                                                                                 idx->medoid, d_entry);
             st = cuda_status(cudaGetLastError());
         }
     }

@@ -59,6 +59,7 @@ struct SearchLaunch {
     size_t scratch_bytes;
     int max_teams;  // cap on the persistent grid (0 = occupancy-limited only)
     int64_t qdiv;   // work item i uses query row and target i / qdiv (0 = 1)
+    int n_entries;  // seeds per work item in entries[] (0 = 1)
 };
 
 // Queues the beam-search kernel (search.cu).

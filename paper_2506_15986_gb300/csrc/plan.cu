@@ -46,7 +46,8 @@ ann_status ann_plan_create(ann_index *idx, const void *d_queries, int64_t nq, in
     if (st == ANN_OK) {
         const int32_t *entry = nullptr;
         if (entry_mode != ANN_ENTRY_MEDOID) {
-            st2 = ann_select_entry(idx, d_queries, nq, entry_mode, L_hub, d_entry_buf, nullptr, s);
+            st2 = ann_select_entries(idx, d_queries, nq, entry_mode, L_hub, p->n_entries > 1 ? p->n_entries : 1,
+                                     d_entry_buf, nullptr, s);
             entry = d_entry_buf;
         }
         if (st2 == ANN_OK)

@@ -53,6 +53,8 @@ struct SearchArgs {
     const int32_t *entries;
     int32_t medoid;
     int L, k, W;
+    int n_entries;   // seeds per query in entries[] (1 when entries is null: the medoid)
+    int fault_wait;  // fault injection: every bulk-copy wait gives up at once
     const int32_t *dk, *dL, *dtarget;
     int32_t *out_ids;
     void *out_dists;
@@ -355,10 +357,13 @@ __global__ void __launch_bounds__(32 * kMaxSearchWarps) beam_search_kernel(const
         const int kq = a.dk ? a.dk[qi] : a.k;
         const int64_t qrow = qi / a.qdiv;
         const int32_t target = a.dtarget ? a.dtarget[qrow] : -1;
-        const int32_t entry = a.entries ? a.entries[qi] : a.medoid;
+        // seed set: lane e < n_entries holds seed e (-1 = unused slot)
+        const int32_t seed = a.entries ? (lane < a.n_entries ? a.entries[qi * a.n_entries + lane] : -1)
+                                       : (lane == 0 ? a.medoid : -1);
+        const bool seeds_ok = !__any_sync(kFull, seed < -1 || seed >= a.n) && __any_sync(kFull, seed >= 0);
         bool failed = false;
-        bool timed_out = false;
-        if (Lq < 1 || Lq > a.L || kq < 1 || kq > a.k || kq > Lq || entry < 0 || entry >= a.n) {
+        bool timed_out = false, lost = false;
+        if (Lq < 1 || Lq > a.L || kq < 1 || kq > a.k || kq > Lq || !seeds_ok) {
             failed = true;
             if (lane == 0)
                 atomicOr(a.status, kStatusBadInputBit);
@@ -390,15 +395,15 @@ __global__ void __launch_bounds__(32 * kMaxSearchWarps) beam_search_kernel(const
                 for (int o = lane; o < (1 << a.spill_bits) / 4; o += 32)
                     reinterpret_cast<uint4 *>(gtab1)[o] = make_uint4(0u, 0u, 0u, 0u);
             __syncwarp();
-            if (lane == 0) {
-                visit(htab, a.hash_bits, !shared_tab, gtab1, a.spill_bits, entry);
-                cbuf[0] = static_cast<uint64_t>(entry) << 1;
-            }
-            used = 1;
-            evals = 1;
-            found = (entry == target);
+            // the initial pool: every distinct seed, evaluated in the first step
+            const int r = seed >= 0 ? visit(htab, a.hash_bits, !shared_tab, gtab1, a.spill_bits, seed) : 0;
+            const unsigned nm = __ballot_sync(kFull, r == 1);
+            if (r == 1)
+                cbuf[__popc(nm & lanemask_lt())] = static_cast<uint64_t>(seed) << 1;
+            used = evals = __popc(nm);
+            found = __any_sync(kFull, r == 1 && seed == target);
         }
-        int nc = failed ? 0 : 1;
+        int nc = failed ? 0 : evals;
         __syncwarp();
 
         while (!failed) {
@@ -416,10 +421,16 @@ __global__ void __launch_bounds__(32 * kMaxSearchWarps) beam_search_kernel(const
                         bulk_g2s(stage + j * a.stage_stride,
                                  a.base + static_cast<size_t>(key_id(cbuf[c0 + j])) * a.rowbytes,
                                  a.rowbytes, bar);
-                    bool ok = mbar_wait_bounded(bar, phase, kTimeoutIters);
+                    const bool ok = !a.fault_wait && mbar_wait_bounded(bar, phase, kTimeoutIters);
                     if (!__all_sync(kFull, ok)) {
-                        // give the copies one more bounded chance, then retire this team
-                        mbar_wait_bounded(bar, phase, kTimeoutIters);
+                        // the query fails with a timeout; give the copies one
+                        // more bounded wait: if they land, the barrier is in a
+                        // known state and the team goes on with the next
+                        // query, else it retires
+                        const bool landed = __all_sync(kFull, mbar_wait_bounded(bar, phase, kTimeoutIters));
+                        if (landed)
+                            phase ^= 1u;
+                        lost = !landed;
                         timed_out = true;
                         failed = true;
                         break;
@@ -696,7 +707,7 @@ __global__ void __launch_bounds__(32 * kMaxSearchWarps) beam_search_kernel(const
             a.out_stats[2 * qi + 1] = miss && target >= 0 ? INT32_MAX : hops;
         }
         __syncwarp();
-        if (timed_out)
+        if (lost)
             return;  // this team's barrier state is unknown: retire it
     }
 }
@@ -874,6 +885,8 @@ ann_status launch_search(ann_index *idx, const SearchLaunch &L, cudaStream_t s)
     a.L = p->L;
     a.k = p->k;
     a.W = p->W;
+    a.n_entries = L.n_entries > 0 ? L.n_entries : 1;
+    a.fault_wait = (p->flags & ANN_SEARCH_FAULT_WAIT) != 0;
     a.dk = p->d_k;
     a.dL = p->d_L;
     a.dtarget = p->d_target;

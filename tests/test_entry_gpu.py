@@ -173,3 +173,49 @@ def test_learned_entry_drives_search(setup):
     oi, od, oe, oh = oracle.search(setup["base"], setup["graph"], setup["q"].astype(np.float64),
                                    ent, 64, 10)
     assert st == ann.OK and (ids == oi).mean() >= 0.999
+
+
+def _select_m(s, mode, m, L_hub=32):
+    nq = len(s["q"])
+    dq = torch.from_numpy(s["q"]).to(DEV)
+    ent = torch.full((nq, m), -7, dtype=torch.int32, device=DEV)
+    ann.ann_select_entries(s["h"], dq, nq, mode, L_hub, m, ent)
+    assert ann.ann_sync_status(s["h"]) == ann.OK
+    return ent.cpu().numpy()
+
+
+@pytest.mark.parametrize("m", [1, 2, 4])
+def test_exhaustive_top_m_hubs(setup, m):
+    # the m best hubs by the scores the tensor cores see, best first; one
+    # seed is exactly the single-entry selection
+    ent = _select_m(setup, ann.ENTRY_LEARNED_EXHAUSTIVE, m)
+    e1, qh = _select(setup, ann.ENTRY_LEARNED_EXHAUSTIVE)
+    assert np.array_equal(ent[:, 0], e1)
+    S = ot.bf16_round(qh) @ _eb(setup["W"][4]).T
+    hub_of = {int(n): i for i, n in enumerate(setup["hub_nodes"])}
+    got = np.array([[S[i, hub_of[int(x)]] for x in row] for i, row in enumerate(ent)])
+    ref = -np.sort(-S, axis=1)[:, :m]
+    assert (np.abs(got - ref)).max() <= 1e-4       # the m best scores, in order
+    assert all(len(set(row)) == m for row in ent)  # m distinct hubs
+
+
+def test_nav_top_m_hubs(setup):
+    ent = _select_m(setup, ann.ENTRY_LEARNED_NAV, 3, L_hub=24)
+    e1, _ = _select(setup, ann.ENTRY_LEARNED_NAV, L_hub=24)
+    assert np.array_equal(ent[:, 0], e1)
+    Eb = _eb(setup["W"][4]).astype(np.float32)
+    ref_q = _oracle_qhat(setup["q"], setup["W"])
+    oi, _, _, _ = oracle.search(Eb, setup["adj"], ref_q, setup["ent"], 24, 3, metric=oracle.IP)
+    hubs = np.asarray(setup["hub_nodes"])
+    assert (ent == hubs[oi]).mean() >= 0.99
+
+
+def test_seed_sets_drive_search(setup):
+    ent = _select_m(setup, ann.ENTRY_LEARNED_EXHAUSTIVE, 4)
+    from gpu_util import search
+    ids, d, ev, hp, st = search(setup["h"], setup["q"], 10, 64, entries=ent)
+    oi, od, oe, oh = oracle.search(setup["base"], setup["graph"], setup["q"].astype(np.float64),
+                                   ent, 64, 10)
+    assert st == ann.OK and (ids == oi).mean() >= 0.999
+    ok = ids == oi
+    assert (np.abs(d - od)[ok] / np.maximum(od[ok], 1e-30)).max() <= 1e-5

@@ -164,3 +164,38 @@ def test_label_mode_counters(golden_dir):
     adj2[6] = [5, -1]  # node 7 loses its only in-edge
     _, _, ev, hp = oracle.search(pts, adj2, q, 0, 3, 1, targets=[7])
     assert ev[0] == oracle.INT32_MAX and hp[0] == oracle.INT32_MAX
+
+
+def test_seed_sets():
+    # a seed set generalises the single entry: one seed equals the scalar
+    # entry; unused slots (-1) and repeated seeds change nothing; every
+    # distinct seed is evaluated once and starts in the pool
+    rng = np.random.default_rng(11)
+    base = rng.standard_normal((400, 6)).astype(np.float32)
+    g, _ = oracle.build_graph(base, K=16, R=8)
+    q = rng.standard_normal((12, 6))
+    med = oracle.medoid(base)
+    a = oracle.search(base, g, q, med, 24, 5, W=2)
+    b = oracle.search(base, g, q, np.full((12, 3), [med, -1, med], np.int32), 24, 5, W=2)
+    for u, v in zip(a, b):
+        assert np.array_equal(u, v)
+    # two seeds on a chain 0-1-2-...-7 (points x_i = i), query at 7.2: seeds 0
+    # and 5 are evaluated first; the walk from 5 reaches 6 and 7 while the
+    # pool (L = 2) drops everything behind
+    pts = np.zeros((8, 2), np.float32)
+    pts[:, 0] = np.arange(8)
+    adj = np.full((8, 2), -1, np.int32)
+    for i in range(8):
+        nb = [j for j in (i - 1, i + 1) if 0 <= j < 8]
+        adj[i, :len(nb)] = nb
+    ids, d, ev, hp = oracle.search(pts, adj, np.array([[7.2, 0.0]]), np.array([[0, 5]], np.int32), 2, 2)
+    # step 1 expands 5 (closer): evaluates 4, 6; pool [6, 5]; step 2 expands 6:
+    # evaluates 7; pool [7, 6]; step 3 expands 7: nothing new; step 4 expands
+    # 6 was done -> stop.  evals = 2 seeds + 4, 6, 7 = 5; hops = 3
+    assert ids[0].tolist() == [7, 6]
+    assert np.allclose(d[0], [0.2 ** 2, 1.2 ** 2])
+    assert (int(ev[0]), int(hp[0])) == (5, 3)
+    # L >= N on a connected graph: exact k-NN from any seed set
+    ids, d, _, _ = oracle.search(base, g, q, np.array([[med, 3, 77]] * 12, np.int32), 400, 5)
+    tid, td = oracle.knn(base, q, 5)
+    assert np.array_equal(ids, tid)

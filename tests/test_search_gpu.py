@@ -111,6 +111,20 @@ def test_c1_team_sizes_bit_exact(c1, team, stage_rows):
     assert np.array_equal(d, od.astype(np.int64).astype(np.int32))
 
 
+def test_forced_wait_timeout_is_reported_and_recoverable(c1):
+    # fault injection: every wait for gathered rows gives up at once.  Each
+    # query fails with -1 ids, the call reports a timeout, the copies in
+    # flight still land, and the next normal call on the same index is exact.
+    q = c1["queries"]
+    ids, d, ev, hp, st = search(c1["h"], q, 10, 64, flags=ann.SEARCH_FAULT_WAIT)
+    assert st == ann.ERR_TIMEOUT
+    assert (ids == -1).all() and (d == 2**31 - 1).all()
+    ids, d, ev, hp, st = search(c1["h"], q, 10, 64)
+    oi, od, oe, oh = _oracle(c1, q, 64, 10)
+    assert st == ann.OK
+    assert np.array_equal(ids, oi) and np.array_equal(ev, oe) and np.array_equal(hp, oh)
+
+
 @pytest.mark.parametrize("L,spill_bits,hash_bits", [(128, 0, 8), (512, 10, 8), (128, 0, -1), (512, 10, -1)])
 def test_c1_spill_to_global_table_stays_exact(c1, L, spill_bits, hash_bits):
     # hash_bits=8: 192 shared slots, far fewer than the evaluations, so the
@@ -144,6 +158,24 @@ def test_c1_per_query_entries_k_L(c1):
     assert np.array_equal(ev, oe) and np.array_equal(hp, oh)
 
 
+@pytest.mark.parametrize("m,W", [(2, 1), (4, 4), (32, 2)])
+def test_c1_seed_sets_bit_exact(c1, m, W):
+    # seed sets with unused slots (-1) and repeated seeds: the initial pool
+    # holds every distinct seed, evaluated once
+    rng = np.random.default_rng(m)
+    q = c1["queries"]
+    seeds = rng.integers(0, len(c1["base"]), (len(q), m)).astype(np.int32)
+    seeds[rng.random(seeds.shape) < 0.3] = -1
+    seeds[:, 0] = np.where(seeds[:, 0] < 0, c1["medoid"], seeds[:, 0])
+    if m > 1:
+        seeds[::3, 1] = seeds[::3, 0]  # a repeated seed
+    ids, d, ev, hp, st = search(c1["h"], q, 10, 64, W=W, entries=seeds)
+    oi, od, oe, oh = oracle.search(c1["base"], c1["graph"], q.astype(np.float64), seeds, 64, 10, W=W)
+    assert st == ann.OK
+    assert np.array_equal(ids, oi) and np.array_equal(ev, oe) and np.array_equal(hp, oh)
+    assert np.array_equal(d, od.astype(np.int64).astype(np.int32))
+
+
 def test_c1_label_mode_targets(c1):
     q = c1["queries"][:50]
     t, _ = oracle.knn(c1["base"], q.astype(np.float64), 1)
@@ -169,10 +201,15 @@ def test_empty_batch_and_bad_device_inputs(c1):
     assert ann.ann_sync_status(c1["h"]) == ann.OK  # cleared by the read
     # host-side parameter checks return before any launch
     for kw in (dict(team=3), dict(team=64), dict(stage_rows=33), dict(W=5), dict(hash_bits=7), dict(hash_bits=-2),
-               dict(spill_bits=9), dict(spill_bits=17)):
+               dict(spill_bits=9), dict(spill_bits=17), dict(flags=4),
+               dict(entries=np.zeros((4, 33), np.int32))):
         with pytest.raises(ann.AnnError) as e:
             search(c1["h"], q[:4], 10, 64, **kw)
         assert e.value.status == ann.ERR_INVALID_ARG, kw
+    # a seed row without any node, or with an id out of range, fails on the device
+    for bad in ([-1, -1], [5, len(c1["base"])]):
+        ids, d, ev, hp, st = search(c1["h"], q[:1], 10, 64, entries=np.array([bad], np.int32))
+        assert st == ann.ERR_INVALID_ARG and (ids == -1).all()
 
 
 @pytest.fixture(scope="module")
