@@ -222,7 +222,10 @@ ann_status ann_load_index(const char *path, int device, ann_index **out);
  *   d_stats   out (optional): nq*2 int32 {distance evaluations, expansions}
  * One warp serves one query; queries are pulled from a device work queue by
  * a persistent grid sized to the SM count.  Scratch memory is taken from a
- * stream-ordered pool owned by the index.
+ * stream-ordered pool owned by the index, per call: calls on different
+ * streams may run concurrently on one index (their outputs must not alias),
+ * which lets the next batch's grid fill the SMs that one batch's last
+ * queries leave idle.
  */
 ann_status ann_search_batch(ann_index *idx, const void *d_queries, int64_t nq,
                             const int32_t *d_entry, const ann_search_params *p,
@@ -266,16 +269,24 @@ ann_status ann_plan_free(ann_plan *plan);
  * (stage_rows 4, 8, 12, 16),
  * distance team sizes (team 2 to 32 where a lane gets 1 to 16 16-byte chunks
  * of the row) and first spill-table sizes (spill_bits up to two either side
- * of the default), one after the other, reps runs each after one warm-up, and
- * return in *best the copy of *p with the fastest combination (*best_ms: its
- * mean time).  The visited set stays exact (shared table plus global spill)
- * and the gather order does not enter any result; the team size only moves
- * float distances by FP32 rounding.  Blocking; d_ids / d_dists receive the
- * results of the last run.
+ * of the default), one after the other, and return in *best the copy of *p
+ * with the fastest combination (*best_ms: its time per batch).
+ *   reps   timed batches per combination, after one warm-up batch per lane
+ *   lanes  1..8 streams the timed batches alternate over (batch r on lane
+ *          r mod lanes), so that combinations are timed with consecutive
+ *          batches overlapping, as they run when a caller spreads batches over
+ *          that many streams; lane 0 is `stream`, the others are created and
+ *          destroyed here and write to output buffers from the index's pool
+ *   d_ids, d_dists  out: the results of the chosen combination
+ * The visited set stays exact (shared table plus global spill) and the gather
+ * order does not enter any result; the team size only moves float distances
+ * by FP32 rounding.  Blocking.  Errors: ANN_ERR_INVALID_ARG for a NULL index,
+ * params or best, nq < 1, reps < 1 or lanes outside 1..8; a search error
+ * stops the tuning and is returned.
  */
 ann_status ann_autotune(ann_index *idx, const void *d_queries, int64_t nq, const int32_t *d_entry,
                         const ann_search_params *p, int32_t *d_ids, void *d_dists, int32_t reps,
-                        ann_search_params *best, float *best_ms, void *stream);
+                        int32_t lanes, ann_search_params *best, float *best_ms, void *stream);
 
 /* ---- learned entry selection (Sec. 4.3) ---------------------------------- */
 

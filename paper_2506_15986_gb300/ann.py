@@ -396,17 +396,17 @@ def ann_plan_free(plan):
     _check(lib.ann_plan_free(plan), "ann_plan_free")
 
 
-def ann_autotune(h, queries, nq, entry, params, ids, dists, reps=3, stream=None):
-    """Returns (best ann_search_params, best mean ms)."""
+def ann_autotune(h, queries, nq, entry, params, ids, dists, reps=3, stream=None, lanes=1):
+    """Returns (best ann_search_params, best ms per batch)."""
     lib = load_library()
     lib.ann_autotune.argtypes = [_p, _p, _c.c_int64, _p, _c.POINTER(ann_search_params), _p, _p,
-                                 _c.c_int32, _c.POINTER(ann_search_params),
+                                 _c.c_int32, _c.c_int32, _c.POINTER(ann_search_params),
                                  _c.POINTER(_c.c_float), _p]
     lib.ann_autotune.restype = _c.c_int32
     best = ann_search_params()
     ms = _c.c_float(0.0)
     _check(lib.ann_autotune(h, _ptr(queries), int(nq), _ptr(entry), ctypes.byref(params),
-                            _ptr(ids), _ptr(dists), int(reps), ctypes.byref(best),
+                            _ptr(ids), _ptr(dists), int(reps), int(lanes), ctypes.byref(best),
                             ctypes.byref(ms), _stream(stream)), "ann_autotune")
     return best, ms.value
 

@@ -93,18 +93,50 @@ ann_status ann_plan_free(ann_plan *plan)
 }
 
 ann_status ann_autotune(ann_index *idx, const void *d_queries, int64_t nq, const int32_t *d_entry,
-                        const ann_search_params *p, int32_t *d_ids, void *d_dists, int32_t reps,
+                        const ann_search_params *p, int32_t *d_ids, void *d_dists, int32_t reps, int32_t lanes,
                         ann_search_params *best, float *best_ms, void *stream)
 {
-    if (!idx || !p || !best || nq < 1 || reps < 1)
+    if (!idx || !p || !best || nq < 1 || reps < 1 || lanes < 1 || lanes > 8 || p->k < 1)
         return ANN_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     int prev = 0;
     cudaGetDevice(&prev);
     cudaSetDevice(idx->device);
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
+    ann_status st = ANN_OK;
+    // lane 0 is the caller's stream and buffers; every other lane has its own
+    // stream and output buffers from the index's pool
+    std::vector<cudaStream_t> ls(lanes, s);
+    std::vector<cudaEvent_t> joins(lanes, nullptr);
+    std::vector<int32_t *> lids(lanes, d_ids);
+    std::vector<void *> ldists(lanes, d_dists);
+    cudaEvent_t e0 = nullptr, e1 = nullptr, fork = nullptr;
+    void *extra = nullptr;
+    const size_t ob = static_cast<size_t>(nq) * p->k * 4;  // ids; distances are 4 bytes for every dtype
+    st = cuda_status(cudaEventCreate(&e0));
+    if (st == ANN_OK)
+        st = cuda_status(cudaEventCreate(&e1));
+    if (st == ANN_OK)
+        st = cuda_status(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    if (st == ANN_OK && lanes > 1)
+        st = scratch_alloc(idx, 2 * ob * (lanes - 1), s, &extra);
+    for (int i = 1; i < lanes && st == ANN_OK; ++i) {
+        st = cuda_status(cudaStreamCreateWithFlags(&ls[i], cudaStreamNonBlocking));
+        if (st == ANN_OK)
+            st = cuda_status(cudaEventCreateWithFlags(&joins[i], cudaEventDisableTiming));
+        lids[i] = reinterpret_cast<int32_t *>(static_cast<uint8_t *>(extra) + 2 * ob * (i - 1));
+        ldists[i] = static_cast<uint8_t *>(extra) + 2 * ob * (i - 1) + ob;
+    }
+    // the other lanes start after what the caller's stream holds so far
+    auto fork_lanes = [&](cudaEvent_t ev) {
+        for (int i = 1; i < lanes; ++i)
+            cudaStreamWaitEvent(ls[i], ev, 0);
+    };
+    auto join_lanes = [&]() {
+        for (int i = 1; i < lanes; ++i) {
+            cudaEventRecord(joins[i], ls[i]);
+            cudaStreamWaitEvent(s, joins[i], 0);
+        }
+    };
     // visited-table sizes around the default, and gather round sizes
     int hb0 = 10;
     while ((1 << hb0) * 3 / 4 < 12 * p->L && hb0 < 13)
@@ -116,10 +148,14 @@ ann_status ann_autotune(ann_index *idx, const void *d_queries, int64_t nq, const
     const int srs[] = {4, 8, 12, 16};
     float bms = 1e30f;
     ann_search_params bp = *p;
-    ann_status st = ANN_OK;
-    // times one candidate; false on a hard error (st set)
+    // times one candidate: reps batches, batch r on lane r mod lanes; false on
+    // a hard error (st set)
     auto trial = [&](const ann_search_params &c) -> bool {
-        st = ann_search_batch(idx, d_queries, nq, d_entry, &c, d_ids, d_dists, nullptr, s);  // warm-up
+        cudaEventRecord(fork, s);
+        fork_lanes(fork);
+        for (int i = 0; i < lanes && st == ANN_OK; ++i)  // warm-up
+            st = ann_search_batch(idx, d_queries, nq, d_entry, &c, lids[i], ldists[i], nullptr, ls[i]);
+        join_lanes();
         if (st == ANN_ERR_UNSUPPORTED) {  // does not fit in shared memory
             st = ANN_OK;
             return true;
@@ -127,8 +163,11 @@ ann_status ann_autotune(ann_index *idx, const void *d_queries, int64_t nq, const
         if (st != ANN_OK)
             return false;
         cudaEventRecord(e0, s);
+        fork_lanes(e0);
         for (int r = 0; r < reps && st == ANN_OK; ++r)
-            st = ann_search_batch(idx, d_queries, nq, d_entry, &c, d_ids, d_dists, nullptr, s);
+            st = ann_search_batch(idx, d_queries, nq, d_entry, &c, lids[r % lanes], ldists[r % lanes], nullptr,
+                                  ls[r % lanes]);
+        join_lanes();
         cudaEventRecord(e1, s);
         if (st != ANN_OK)
             return false;
@@ -145,19 +184,17 @@ ann_status ann_autotune(ann_index *idx, const void *d_queries, int64_t nq, const
         }
         return true;
     };
+    bool ok = st == ANN_OK;
     // stage 1: visited-table size x gather round size at the given team size
-    bool ok = true;
-    for (int hb : hbs) {
+    for (size_t h = 0; ok && h < hbs.size(); ++h) {
         for (int sr : srs) {
             ann_search_params c = *p;
-            c.hash_bits = hb;
+            c.hash_bits = hbs[h];
             c.stage_rows = sr;
             c.team = p->team > 0 ? p->team : ann::default_team(idx->rowbytes);
             if (!(ok = trial(c)))
                 break;
         }
-        if (!ok)
-            break;
     }
     // stage 2: team sizes at the best pair, from 1 to 16 chunks of the row per lane
     const int chunks = idx->rowbytes / 16;
@@ -181,8 +218,27 @@ ann_status ann_autotune(ann_index *idx, const void *d_queries, int64_t nq, const
         c.spill_bits = sb;
         ok = trial(c);
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    // the caller's outputs hold the chosen combination's results
+    if (ok && bms < 1e30f)
+        st = ann_search_batch(idx, d_queries, nq, d_entry, &bp, d_ids, d_dists, nullptr, s);
+    for (int i = 1; i < lanes; ++i)
+        if (ls[i] != s) {
+            cudaStreamSynchronize(ls[i]);
+            cudaStreamDestroy(ls[i]);
+        }
+    if (extra)
+        scratch_free(idx, extra, s);
+    if (st == ANN_OK)
+        st = cuda_status(cudaStreamSynchronize(s));
+    for (int i = 1; i < lanes; ++i)
+        if (joins[i])
+            cudaEventDestroy(joins[i]);
+    if (fork)
+        cudaEventDestroy(fork);
+    if (e0)
+        cudaEventDestroy(e0);
+    if (e1)
+        cudaEventDestroy(e1);
     cudaSetDevice(prev);
     if (st != ANN_OK)
         return st;

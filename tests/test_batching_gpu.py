@@ -91,7 +91,8 @@ def test_graph_plan_replays_the_batch(case, mode):
     assert ann.ann_sync_status(case["h"]) == ann.OK
 
 
-def test_autotune_keeps_results(case):
+@pytest.mark.parametrize("lanes", [1, 3])
+def test_autotune_keeps_results(case, lanes):
     q = _t(case["queries"])
     nq = q.shape[0]
     p = ann.search_params(10, 128)
@@ -99,11 +100,14 @@ def test_autotune_keeps_results(case):
     dd = torch.empty((nq, 10), dtype=torch.float32, device=DEV)
     ann.ann_search_batch(case["h"], q, nq, None, p, ids, dd)
     ref = ids.clone(), dd.clone()
-    best, ms = ann.ann_autotune(case["h"], q, nq, None, p, ids, dd, reps=2)
+    ids.fill_(-7)
+    best, ms = ann.ann_autotune(case["h"], q, nq, None, p, ids, dd, reps=3, lanes=lanes)
     assert ms > 0 and (best.hash_bits >= 8 or best.hash_bits == -1) and best.stage_rows in (4, 8, 12, 16)
     assert best.team in (2, 4, 8, 16, 32) and best.spill_bits in (0, 10, 11, 12, 13, 14, 15, 16)
+    tuned = ids.clone(), dd.clone()  # the autotuner leaves the chosen combination's results
     ann.ann_search_batch(case["h"], q, nq, None, best, ids, dd)
     torch.cuda.synchronize()
+    assert torch.equal(ids, tuned[0]) and torch.equal(dd, tuned[1])
     # the visited-table and gather sizes never change results: equal to a
     # run with the default knobs at the same team size
     same = ann.search_params(10, 128, team=best.team)
@@ -117,3 +121,45 @@ def test_autotune_keeps_results(case):
     ok = a == b
     da, db = dd.cpu().numpy()[ok].astype(np.float64), ref[1].cpu().numpy()[ok].astype(np.float64)
     assert (np.abs(da - db) <= 1e-5 * np.abs(db)).all()
+
+
+def test_autotune_rejects_bad_lanes(case):
+    q = _t(case["queries"][:8])
+    ids = torch.empty((8, 10), dtype=torch.int32, device=DEV)
+    dd = torch.empty((8, 10), dtype=torch.float32, device=DEV)
+    for bad in (0, 9):
+        with pytest.raises(ann.AnnError) as e:
+            ann.ann_autotune(case["h"], q, 8, None, ann.search_params(10, 64), ids, dd, lanes=bad)
+        assert e.value.status == ann.ERR_INVALID_ARG
+
+
+def test_concurrent_batches_on_lanes(case):
+    # consecutive batches on separate streams overlap on the device; each call
+    # takes its own stream-ordered scratch, so the results equal one batch at a
+    # time on one stream
+    q = case["queries"]
+    nq = len(q)
+    p = ann.search_params(10, 96)
+    halves = [_t(q[: nq // 2]), _t(q[nq // 2:])]
+    ref = []
+    for dq in halves:
+        ids = torch.empty((dq.shape[0], 10), dtype=torch.int32, device=DEV)
+        dd = torch.empty((dq.shape[0], 10), dtype=torch.float32, device=DEV)
+        ann.ann_search_batch(case["h"], dq, dq.shape[0], None, p, ids, dd)
+        torch.cuda.synchronize()
+        ref.append((ids.cpu().numpy(), dd.cpu().numpy()))
+    lanes = [torch.cuda.Stream(device=DEV) for _ in range(3)]
+    outs = []
+    for rep in range(4):
+        for j, dq in enumerate(halves):
+            s = lanes[(2 * rep + j) % 3]
+            with torch.cuda.stream(s):
+                ids = torch.empty((dq.shape[0], 10), dtype=torch.int32, device=DEV)
+                dd = torch.empty((dq.shape[0], 10), dtype=torch.float32, device=DEV)
+            ann.ann_search_batch(case["h"], dq, dq.shape[0], None, p, ids, dd, None, s)
+            outs.append((j, ids, dd))
+    torch.cuda.synchronize()
+    assert ann.ann_sync_status(case["h"]) == ann.OK
+    for j, ids, dd in outs:
+        assert np.array_equal(ids.cpu().numpy(), ref[j][0])
+        assert np.array_equal(dd.cpu().numpy(), ref[j][1])
