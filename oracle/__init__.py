@@ -64,6 +64,8 @@ def _lib():
         lib.or_kmeans.restype = i32
         lib.or_hubs.argtypes = [p, i64, i32, i32, p, i32, p, p, i32]
         lib.or_hubs.restype = i32
+        lib.or_hbkm.argtypes = [p, i64, i32, i32, i32, dbl, i32, p, p, p, p, p]
+        lib.or_hbkm.restype = i32
         lib.or_hub_graph.argtypes = [p, i32, i32, i32, p, p]
         lib.or_hub_graph.restype = i32
         lib.or_num_threads.argtypes = []
@@ -202,6 +204,28 @@ def hubs(base, centroids, threads=None):
     if rc:
         raise RuntimeError(f"or_hubs failed ({rc})")
     return h, a
+
+
+def hbkm(x, k, levels, lam, T, keys):
+    """Hierarchical balanced k-means (Sec. 4.1, Def. 2, Algorithm 2) and the
+    hub of every final cluster (Def. 3), float32 as or_hbkm states.  keys:
+    one uint32 per row, the seeded draw that picks each split's initial
+    centroids.  Returns (label [n], centroids float32 [k^levels, d],
+    hubs [k^levels] (-1 = empty), sizes [k^levels])."""
+    x = np.ascontiguousarray(x, np.float32)
+    n, d = x.shape
+    keys = np.ascontiguousarray(keys, np.uint32)
+    assert keys.shape == (n,)
+    nc = int(k) ** int(levels)
+    label = np.empty(n, np.int32)
+    cent = np.empty((nc, d), np.float32)
+    hubs = np.empty(nc, np.int32)
+    sizes = np.empty(nc, np.int64)
+    rc = _lib().or_hbkm(_ptr(x), n, d, int(k), int(levels), float(lam), int(T), _ptr(keys),
+                        _ptr(label), _ptr(cent), _ptr(hubs), _ptr(sizes))
+    if rc:
+        raise RuntimeError(f"or_hbkm failed ({rc})")
+    return label, cent, hubs, sizes
 
 
 def hub_graph(emb, s):

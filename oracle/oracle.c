@@ -11,8 +11,9 @@
  * int8 codes with a per-row scale: code * scale is exact in double).
  *
  * Arithmetic: every floating-point distance is accumulated in double
- * precision; uint8 data give integer squared distances that double holds
- * exactly (128 * 255^2 < 2^53).  Every ordering is the lexicographic order on
+ * precision (or_hbkm excepted: it decides cluster memberships in float32,
+ * the precision the GPU decides them in); uint8 data give integer squared
+ * distances that double holds exactly (128 * 255^2 < 2^53).  Every ordering is the lexicographic order on
  * (distance, id), smaller id first on ties.
  *
  * Functions and the passages they follow:
@@ -26,8 +27,11 @@
  *                      reachability repair from the navigating node
  *   or_medoid          navigating node of the NSG-style graph (Sec. 2.1): the
  *                      base point nearest the data mean
- *   or_kmeans          Lloyd's k-means (flat stand-in for the balanced
+ *   or_kmeans          Lloyd's k-means (the flat alternative to the balanced
  *                      clustering of Sec. 4.1, Def. 2 / Algorithm 2)
+ *   or_hbkm            hierarchical balanced k-means (Sec. 4.1, Def. 2,
+ *                      Algorithm 2) and its hubs (Def. 3), with the readings
+ *                      listed at the function; float32 (see there)
  *   or_hubs            hub nodes (Sec. 4.1, Def. 3): in each cluster, the
  *                      member nearest its centroid
  *   or_hub_graph       high-tier hub graph (Sec. 4.3): each hub linked to its
@@ -758,4 +762,194 @@ int or_num_threads(void)
 #else
     return 1;
 #endif
+}
+
+/* ------------------------------------------------------------------------ */
+/* Hierarchical balanced k-means, HBKM (Sec. 4.1, Def. 2 and Algorithm 2),   */
+/* and the hub of every final cluster (Def. 3).                              */
+/*                                                                           */
+/* Each of `levels` rounds splits every cluster C of the previous round      */
+/* (round 0: the whole data set) into k children, so k^levels clusters come  */
+/* out.  A split runs T iterations; each iteration empties the children,     */
+/* then visits C's members in increasing id and puts member x into           */
+/*   j = argmin_j ||x - mu_j||^2 + lam * (2 (c_j - m) + 1)                   */
+/* (ties to the smaller j), c_j the child's current size and m = |C| / k;    */
+/* the penalty is the increase of Def. 2's size-variance objective           */
+/* (c_j + 1 - m)^2 - (c_j - m)^2 that adding x to child j causes, and        */
+/* lam = lambda * sigma^2 / m with sigma^2 the mean squared distance of C's  */
+/* members to C's centroid, so that lambda carries no units.  After the      */
+/* visit every non-empty child's centroid becomes the mean of its members    */
+/* (an empty child keeps its centroid).  The children start at the members  */
+/* with the min(k, |C|) smallest (key, id), in that order; children past |C| */
+/* stay empty.  Child j of cluster c is cluster c * k + j of the next round. */
+/*                                                                           */
+/* Arithmetic is float32 with every operation rounded on its own (the        */
+/* file's build keeps floating-point contraction off), in these orders:      */
+/* distance = sum over coordinates 0..d-1 of (x_t - mu_t)^2; sigma^2 and     */
+/* the centroid sums run over members in increasing id; division last.      */
+/* Float32 is the precision in which the assignment (an integer) is decided. */
+/*                                                                           */
+/* Outputs: label[n] final cluster of every row; centroids[k^levels * d];    */
+/* hubs[k^levels], the member nearest its cluster's centroid (smaller id on  */
+/* ties), -1 for an empty cluster; sizes (optional) the final cluster sizes. */
+/* ------------------------------------------------------------------------ */
+static float hb_dist(const float *x, const float *mu, int d)
+{
+    float acc = 0.0f;
+    for (int t = 0; t < d; ++t) {
+        const float df = x[t] - mu[t];
+        const float sq = df * df;
+        acc = acc + sq;
+    }
+    return acc;
+}
+
+int or_hbkm(const float *x, int64_t n, int d, int k, int levels, double lambda, int T,
+            const uint32_t *keys, int32_t *label, float *centroids, int32_t *hubs, int64_t *sizes)
+{
+    if (!x || !keys || !label || !centroids || !hubs || n <= 0 || d <= 0 || k < 2 || levels < 1 || T < 1 ||
+        lambda < 0.0)
+        return OR_ERR_ARG;
+    int64_t nc = 1;
+    for (int l = 0; l < levels; ++l) {
+        nc *= k;
+        if (nc > (int64_t)1 << 30)
+            return OR_ERR_ARG;
+    }
+    float *cur = (float *)malloc(sizeof(float) * (size_t)d);  /* round-0 centroid */
+    float *pc = NULL;                                        /* parents' centroids */
+    float *cc = NULL;                                        /* children's centroids */
+    int32_t *own = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t *nown = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t *mem = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);  /* a cluster's members */
+    int32_t *chl = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);  /* their child index */
+    int64_t *cnt = (int64_t *)malloc(sizeof(int64_t) * (size_t)k);
+    int32_t *ini = (int32_t *)malloc(sizeof(int32_t) * (size_t)k);
+    float *sum = (float *)malloc(sizeof(float) * (size_t)k * d);
+    if (!cur || !own || !nown || !mem || !chl || !cnt || !ini || !sum) {
+        free(cur); free(own); free(nown); free(mem); free(chl); free(cnt); free(ini); free(sum);
+        return OR_ERR_NOMEM;
+    }
+    /* round 0: one cluster, the data set, with its mean */
+    for (int t = 0; t < d; ++t) {
+        float s = 0.0f;
+        for (int64_t i = 0; i < n; ++i)
+            s = s + x[i * (int64_t)d + t];
+        cur[t] = s / (float)n;
+    }
+    for (int64_t i = 0; i < n; ++i)
+        own[i] = 0;
+    pc = cur;
+    int64_t np = 1;
+    int err = OR_OK;
+    for (int l = 1; l <= levels && err == OR_OK; ++l) {
+        cc = (float *)malloc(sizeof(float) * (size_t)(np * k) * d);
+        if (!cc) {
+            err = OR_ERR_NOMEM;
+            break;
+        }
+        for (int64_t c = 0; c < np; ++c) {
+            const float *mu_p = pc + c * d;
+            float *mu = cc + c * k * d;
+            /* members of cluster c in increasing id */
+            int64_t s = 0;
+            for (int64_t i = 0; i < n; ++i)
+                if (own[i] == c)
+                    mem[s++] = (int32_t)i;
+            /* every child starts at the parent's centroid (what an empty child keeps) */
+            for (int j = 0; j < k; ++j)
+                memcpy(mu + (int64_t)j * d, mu_p, sizeof(float) * (size_t)d);
+            if (s == 0)
+                continue;
+            /* penalty scale */
+            float sig = 0.0f;
+            for (int64_t a = 0; a < s; ++a)
+                sig = sig + hb_dist(x + (int64_t)mem[a] * d, mu_p, d);
+            sig = sig / (float)s;
+            const float m = (float)s / (float)k;
+            const float lam = ((float)lambda * sig) / m;
+            /* initial centroids: the members with the smallest (key, id) */
+            const int kk = s < k ? (int)s : k;
+            for (int j = 0; j < kk; ++j) {
+                int32_t best = -1;
+                for (int64_t a = 0; a < s; ++a) {
+                    const int32_t id = mem[a];
+                    int taken = 0;
+                    for (int q = 0; q < j; ++q)
+                        taken |= ini[q] == id;
+                    if (taken)
+                        continue;
+                    if (best < 0 || keys[id] < keys[best] || (keys[id] == keys[best] && id < best))
+                        best = id;
+                }
+                ini[j] = best;
+                memcpy(mu + (int64_t)j * d, x + (int64_t)best * d, sizeof(float) * (size_t)d);
+            }
+            for (int it = 0; it < T; ++it) {
+                for (int j = 0; j < k; ++j)
+                    cnt[j] = 0;
+                for (int64_t a = 0; a < s; ++a) {
+                    const float *xa = x + (int64_t)mem[a] * d;
+                    int bj = -1;
+                    float bc = 0.0f;
+                    for (int j = 0; j < kk; ++j) {
+                        const float pen = lam * (2.0f * ((float)cnt[j] - m) + 1.0f);
+                        const float cost = hb_dist(xa, mu + (int64_t)j * d, d) + pen;
+                        if (bj < 0 || cost < bc) {
+                            bj = j;
+                            bc = cost;
+                        }
+                    }
+                    chl[a] = bj;
+                    cnt[bj]++;
+                }
+                for (int64_t q = 0; q < (int64_t)k * d; ++q)
+                    sum[q] = 0.0f;
+                for (int64_t a = 0; a < s; ++a)
+                    for (int t = 0; t < d; ++t)
+                        sum[(int64_t)chl[a] * d + t] = sum[(int64_t)chl[a] * d + t] + x[(int64_t)mem[a] * d + t];
+                for (int j = 0; j < kk; ++j)
+                    if (cnt[j] > 0)
+                        for (int t = 0; t < d; ++t)
+                            mu[(int64_t)j * d + t] = sum[(int64_t)j * d + t] / (float)cnt[j];
+            }
+            for (int64_t a = 0; a < s; ++a)
+                nown[mem[a]] = (int32_t)(c * k + chl[a]);
+        }
+        memcpy(own, nown, sizeof(int32_t) * (size_t)n);
+        if (pc != cur)
+            free(pc);
+        pc = cc;
+        cc = NULL;
+        np *= k;
+    }
+    if (err == OR_OK) {
+        memcpy(centroids, pc, sizeof(float) * (size_t)nc * d);
+        for (int64_t c = 0; c < nc; ++c) {
+            hubs[c] = -1;
+            if (sizes)
+                sizes[c] = 0;
+        }
+        float *hd = (float *)malloc(sizeof(float) * (size_t)nc);
+        if (!hd) {
+            err = OR_ERR_NOMEM;
+        } else {
+            for (int64_t i = 0; i < n; ++i) {
+                const int64_t c = own[i];
+                label[i] = (int32_t)c;
+                if (sizes)
+                    sizes[c]++;
+                const float di = hb_dist(x + i * (int64_t)d, pc + c * d, d);
+                if (hubs[c] < 0 || di < hd[c]) {  /* increasing id: the first of equals stays */
+                    hubs[c] = (int32_t)i;
+                    hd[c] = di;
+                }
+            }
+            free(hd);
+        }
+    }
+    if (pc != cur)
+        free(pc);
+    free(cc); free(cur); free(own); free(nown); free(mem); free(chl); free(cnt); free(ini); free(sum);
+    return err;
 }

@@ -196,6 +196,13 @@ def kmeans_init(m, k, seed):
     return _rng(seed).permutation(m)[:k].astype(np.int32)
 
 
+def hbkm_keys(n, seed):
+    """One uniform uint32 key per row: the draw from which hierarchical
+    balanced k-means takes each split's initial centroids (the members with
+    the smallest keys)."""
+    return _rng(seed).integers(0, 2**32, size=n, dtype=np.uint64).astype(np.uint32)
+
+
 def sample_rows(n, m, seed):
     """m distinct row indices out of n, sorted (k-means training sample)."""
     if m >= n:
