@@ -66,6 +66,8 @@ def _lib():
         lib.or_hubs.restype = i32
         lib.or_hbkm.argtypes = [p, i64, i32, i32, i32, dbl, i32, p, p, p, p, p]
         lib.or_hbkm.restype = i32
+        lib.or_topo_tokens.argtypes = [p, i64, i32, p, i32, p, i32, i32, i32, p, p]
+        lib.or_topo_tokens.restype = i32
         lib.or_hub_graph.argtypes = [p, i32, i32, i32, p, p]
         lib.or_hub_graph.restype = i32
         lib.or_num_threads.argtypes = []
@@ -226,6 +228,27 @@ def hbkm(x, k, levels, lam, T, keys):
     if rc:
         raise RuntimeError(f"or_hbkm failed ({rc})")
     return label, cent, hubs, sizes
+
+
+TOKEN_DIM = 8
+
+
+def topo_tokens(base, graph, hubs, h, max_nodes=4096):
+    """Per-hop topology tokens of each hub from the guided subgraph walk
+    (Sec. 4.2), float32 as or_topo_tokens states.  Returns (tokens
+    float32 [H, h+1, 8], subgraph sizes [H])."""
+    x = np.ascontiguousarray(base, np.float32)
+    n, d = x.shape
+    g = np.ascontiguousarray(graph, np.int32)
+    hubs = np.ascontiguousarray(hubs, np.int32)
+    H = len(hubs)
+    tok = np.empty((H, h + 1, TOKEN_DIM), np.float32)
+    nodes = np.empty(H, np.int32)
+    rc = _lib().or_topo_tokens(_ptr(x), n, d, _ptr(g), g.shape[1], _ptr(hubs), H, int(h), int(max_nodes),
+                               _ptr(tok), _ptr(nodes))
+    if rc:
+        raise RuntimeError(f"or_topo_tokens failed ({rc})")
+    return tok, nodes
 
 
 def hub_graph(emb, s):

@@ -13,7 +13,8 @@
  * Arithmetic: every floating-point distance is accumulated in double
  * precision (or_hbkm excepted: it decides cluster memberships in float32,
  * the precision the GPU decides them in); uint8 data give integer squared
- * distances that double holds exactly (128 * 255^2 < 2^53).  Every ordering is the lexicographic order on
+ * distances that double holds exactly (128 * 255^2 < 2^53).  or_topo_tokens
+ * ranks neighbours in float32 for the same reason as or_hbkm.  Every ordering is the lexicographic order on
  * (distance, id), smaller id first on ties.
  *
  * Functions and the passages they follow:
@@ -34,6 +35,8 @@
  *                      listed at the function; float32 (see there)
  *   or_hubs            hub nodes (Sec. 4.1, Def. 3): in each cluster, the
  *                      member nearest its centroid
+ *   or_topo_tokens     per-hop topology tokens of each hub from the guided
+ *                      subgraph walk of Sec. 4.2 (float32, see there)
  *   or_hub_graph       high-tier hub graph (Sec. 4.3): each hub linked to its
  *                      s most cosine-similar hubs
  *   (label generation, Sec. 4.2 Def. 4, uses or_search with a target id)
@@ -952,4 +955,163 @@ int or_hbkm(const float *x, int64_t n, int d, int k, int levels, double lambda, 
         free(pc);
     free(cc); free(cur); free(own); free(nown); free(mem); free(chl); free(cnt); free(ini); free(sum);
     return err;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Topology tokens of a hub (Sec. 4.2, subgraph sampling, with a fixed-size  */
+/* per-hop summary standing in for Graph2Vec).                               */
+/*                                                                           */
+/* The guided walk: MinDeg and MaxDeg are the smallest and largest numbers   */
+/* of valid neighbours over all nodes of G.  A FIFO queue starts with the   */
+/* hub at hop 0.  A dequeued node u at hop < h ranks its deg(u) valid        */
+/* neighbours by (squared L2 to u, id) and samples the ceil(x/2) nearest and */
+/* the floor(x/2) farthest, x = ceil(MinDeg * deg(u) / MaxDeg); each sampled */
+/* neighbour not yet in the subgraph joins it (in rank order) at hop(u) + 1  */
+/* with parent u, and is queued.  Nodes at hop h join but are not expanded;  */
+/* the subgraph stops growing at max_nodes nodes.                            */
+/*                                                                           */
+/* Token l (0..h) summarises the nodes at hop l, with s the hub's mean       */
+/* squared distance to its valid neighbours (1 if it has none or it is 0):   */
+/*   u0 = count / total nodes          u4 = mean d2(w, parent) / s           */
+/*   u1 = mean deg / MaxDeg            u5 = share sampled as farthest        */
+/*   u2 = mean d2(w, hub) / s          u6 = l / h                            */
+/*   u3 = max d2(w, hub) / s           u7 = 1                                */
+/* (u0..u5 are 0 for an empty hop).  float32 as in or_hbkm: distances summed */
+/* over coordinates 0..d-1, means over the hop's nodes in joining order, one */
+/* division at the end; the ranking (an integer decision) uses the same     */
+/* float32 distances the GPU ranks by.                                       */
+/*                                                                           */
+/* tokens: H * (h+1) * 8 floats; nodes (optional): H subgraph sizes.         */
+/* ------------------------------------------------------------------------ */
+#define OR_TOKEN_DIM 8
+
+static float tp_dist(const float *x, int d, int64_t a, int64_t b)
+{
+    return hb_dist(x + a * (int64_t)d, x + b * (int64_t)d, d);
+}
+
+int or_topo_tokens(const float *x, int64_t n, int d, const int32_t *graph, int R, const int32_t *hubs, int H,
+                   int h, int max_nodes, float *tokens, int32_t *nodes)
+{
+    if (!x || !graph || !hubs || !tokens || n <= 0 || d <= 0 || R <= 0 || H <= 0 || h < 1 || max_nodes < 1)
+        return OR_ERR_ARG;
+    int mindeg = R, maxdeg = 0;
+    for (int64_t u = 0; u < n; ++u) {
+        int dg = 0;
+        for (int r = 0; r < R; ++r)
+            dg += graph[u * R + r] >= 0;
+        mindeg = dg < mindeg ? dg : mindeg;
+        maxdeg = dg > maxdeg ? dg : maxdeg;
+    }
+    int32_t *node = (int32_t *)malloc(sizeof(int32_t) * (size_t)max_nodes);
+    int32_t *hop = (int32_t *)malloc(sizeof(int32_t) * (size_t)max_nodes);
+    int32_t *par = (int32_t *)malloc(sizeof(int32_t) * (size_t)max_nodes);
+    uint8_t *far = (uint8_t *)malloc((size_t)max_nodes);
+    int32_t *nb = (int32_t *)malloc(sizeof(int32_t) * (size_t)R);
+    float *nd = (float *)malloc(sizeof(float) * (size_t)R);
+    if (!node || !hop || !par || !far || !nb || !nd) {
+        free(node); free(hop); free(par); free(far); free(nb); free(nd);
+        return OR_ERR_NOMEM;
+    }
+    for (int v = 0; v < H; ++v) {
+        const int32_t hub = hubs[v];
+        float *tok = tokens + (int64_t)v * (h + 1) * OR_TOKEN_DIM;
+        if (hub < 0 || hub >= n) {
+            free(node); free(hop); free(par); free(far); free(nb); free(nd);
+            return OR_ERR_ARG;
+        }
+        int cnt = 1, head = 0;
+        node[0] = hub; hop[0] = 0; par[0] = -1; far[0] = 0;
+        while (head < cnt) {
+            const int32_t u = node[head];
+            const int hu = hop[head];
+            ++head;
+            if (hu >= h)
+                continue;
+            int dg = 0;
+            for (int r = 0; r < R; ++r)
+                if (graph[(int64_t)u * R + r] >= 0) {
+                    nb[dg] = graph[(int64_t)u * R + r];
+                    nd[dg] = tp_dist(x, d, u, nb[dg]);
+                    ++dg;
+                }
+            /* rank by (distance, id): insertion sort */
+            for (int a = 1; a < dg; ++a) {
+                const int32_t ib = nb[a];
+                const float db = nd[a];
+                int b = a;
+                while (b > 0 && (nd[b - 1] > db || (nd[b - 1] == db && nb[b - 1] > ib))) {
+                    nb[b] = nb[b - 1];
+                    nd[b] = nd[b - 1];
+                    --b;
+                }
+                nb[b] = ib;
+                nd[b] = db;
+            }
+            const int xs = maxdeg > 0 ? (mindeg * dg + maxdeg - 1) / maxdeg : 0;
+            const int near_n = (xs + 1) / 2, far_n = xs / 2;
+            for (int a = 0; a < dg && cnt < max_nodes; ++a) {
+                const int is_far = a >= dg - far_n;
+                if (a >= near_n && !is_far)
+                    continue;
+                int seen = 0;
+                for (int q = 0; q < cnt && !seen; ++q)
+                    seen = node[q] == nb[a];
+                if (seen)
+                    continue;
+                node[cnt] = nb[a]; hop[cnt] = hu + 1; par[cnt] = u; far[cnt] = (uint8_t)is_far;
+                ++cnt;
+            }
+        }
+        if (nodes)
+            nodes[v] = cnt;
+        /* scale: the hub's mean squared distance to its valid neighbours */
+        float ssum = 0.0f;
+        int sdeg = 0;
+        for (int r = 0; r < R; ++r) {
+            const int32_t w = graph[(int64_t)hub * R + r];
+            if (w >= 0) {
+                ssum = ssum + tp_dist(x, d, hub, w);
+                ++sdeg;
+            }
+        }
+        float s = sdeg > 0 ? ssum / (float)sdeg : 1.0f;
+        if (!(s > 0.0f))
+            s = 1.0f;
+        for (int l = 0; l <= h; ++l) {
+            float *t = tok + l * OR_TOKEN_DIM;
+            int c = 0, fars = 0;
+            int64_t degsum = 0;
+            float dh = 0.0f, dmax = 0.0f, dpar = 0.0f;
+            for (int q = 0; q < cnt; ++q) {
+                if (hop[q] != l)
+                    continue;
+                const float a = tp_dist(x, d, node[q], hub) / s;
+                const float b = par[q] >= 0 ? tp_dist(x, d, node[q], par[q]) / s : 0.0f;
+                int dg = 0;
+                for (int r = 0; r < R; ++r)
+                    dg += graph[(int64_t)node[q] * R + r] >= 0;
+                ++c;
+                degsum += dg;
+                fars += far[q];
+                dh = dh + a;
+                dmax = a > dmax ? a : dmax;
+                dpar = dpar + b;
+            }
+            for (int f = 0; f < OR_TOKEN_DIM; ++f)
+                t[f] = 0.0f;
+            if (c > 0) {
+                t[0] = (float)c / (float)cnt;
+                t[1] = maxdeg > 0 ? (float)degsum / ((float)c * (float)maxdeg) : 0.0f;
+                t[2] = dh / (float)c;
+                t[3] = dmax;
+                t[4] = dpar / (float)c;
+                t[5] = (float)fars / (float)c;
+            }
+            t[6] = (float)l / (float)h;
+            t[7] = 1.0f;
+        }
+    }
+    free(node); free(hop); free(par); free(far); free(nb); free(nd);
+    return OR_OK;
 }

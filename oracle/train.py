@@ -4,9 +4,10 @@ The two-tower model of Sec. 2.2 / Sec. 4.3 as this project reads it:
 
 * query tower (Sec. 4.3, Module II, "lightweight MLP with ReLU"):
   q -> Z1 = q W1 + b1 -> A1 = ReLU(Z1) -> Z2 = A1 W2 + b2 -> q_hat = Z2 / ||Z2||
-* hub tower: a free embedding table E (one row per hub), e_hat = E / ||E||
-  (stands in for the fusion embedding of Eq. fusion, whose topology features
-  need an external graph-embedding model);
+* hub tower: a free embedding table E (one row per hub), e_hat = E / ||E||;
+  with the topology-aware variant the hub row is E + F, F the fusion
+  embedding of Eq. fusion (Sec. 4.3, Module I) computed from the hub's own
+  vector p and its per-hop topology tokens U (fusion_forward below);
 * similarity sim(q, v) = q_hat . e_hat_v (cosine, Sec. 2.2);
 * loss (Sec. 2.2 Eq. loss and Sec. 4.3 Eq. loss, read per query): with the
   query's positive hubs P and negative hubs N (label mask +1 / -1, 0 = unused),
@@ -124,3 +125,42 @@ def hub_scores_argmax(Qh, Eh):
     S = np.asarray(Qh, np.float64) @ np.asarray(Eh, np.float64).T
     arg = np.argmax(S, axis=1)  # first maximum = smaller index
     return arg.astype(np.int32), S[np.arange(S.shape[0]), arg]
+
+
+def fusion_forward(P, U, WQ, WK, WV, WO, heads):
+    """Fusion embedding, Sec. 4.3 Eq. fusion: per hub, m = heads attention
+    heads of width dk = WQ.shape[1] / heads,
+        F = Concat_j softmax((p WQ_j)(U WK_j)^T / sqrt(dk)) (U WV_j)  WO
+    with p [dp] the hub's vector and U [T, dU] its topology tokens.
+    P [H, dp], U [H, T, dU]; returns (F [H, dF], cache for the backward)."""
+    H, T, _ = U.shape
+    dk = WQ.shape[1] // heads
+    Q = (P @ WQ).reshape(H, heads, dk)
+    K = (U @ WK).reshape(H, T, heads, dk)
+    V = (U @ WV).reshape(H, T, heads, dk)
+    S = np.einsum("hjd,htjd->hjt", Q, K) / np.sqrt(dk)
+    S = S - S.max(axis=2, keepdims=True)
+    A = np.exp(S)
+    A = A / A.sum(axis=2, keepdims=True)
+    O = np.einsum("hjt,htjd->hjd", A, V).reshape(H, heads * dk)
+    return O @ WO, (P, U, Q, K, V, A, O, dk)
+
+
+def fusion_backward(dF, cache, WO):
+    """Gradients of Eq. fusion's weights from dL/dF (summed over hubs):
+    returns (dWQ, dWK, dWV, dWO)."""
+    P, U, Q, K, V, A, O, dk = cache
+    H, heads, _ = Q.shape
+    dWO = O.T @ dF
+    dO = (dF @ WO.T).reshape(H, heads, dk)
+    dA = np.einsum("hjd,htjd->hjt", dO, V)
+    dV = np.einsum("hjt,hjd->htjd", A, dO)
+    dS = A * (dA - (A * dA).sum(axis=2, keepdims=True)) / np.sqrt(dk)
+    dQ = np.einsum("hjt,htjd->hjd", dS, K).reshape(H, heads * dk)
+    dK = np.einsum("hjt,hjd->htjd", dS, Q)
+    T = U.shape[1]
+    Uf = U.reshape(H * T, -1)
+    dWQ = P.T @ dQ
+    dWK = Uf.T @ dK.reshape(H * T, heads * dk)
+    dWV = Uf.T @ dV.reshape(H * T, heads * dk)
+    return dWQ, dWK, dWV, dWO
