@@ -57,6 +57,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+FUSION_HOPS, FUSION_HEADS, FUSION_DK = 5, 4, 16  # h = 5 as in Sec. 5.1; 4 heads of 16
 METRIC = "QPS at recall@10=0.95 on 1 GB300, learned vs medoid entry; dist evals/query"
 L_SWEEP = [16, 24, 32, 40, 48, 56, 64, 72, 80, 88, 96, 112, 128, 144, 160, 176, 192, 224, 256, 320,
            384, 448, 512, 640, 768, 1024, 1536, 2048]
@@ -152,6 +153,14 @@ def parse():
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--W", type=int, default=4, help="pool entries expanded per search step")
     ap.add_argument("--no-tune", action="store_true", help="skip ann_autotune at L*")
+    ap.add_argument("--hbkm", action="store_true",
+                    help="hubs from hierarchical balanced k-means instead of flat k-means")
+    ap.add_argument("--hbkm-lambda", type=float, default=1.0)
+    ap.add_argument("--hbkm-T", type=int, default=10)
+    ap.add_argument("--fusion", action="store_true",
+                    help="topology-aware hub tower: fusion attention over per-hop subgraph tokens")
+    ap.add_argument("--tpos-sweep", action="store_true",
+                    help="also sweep the label rule's t_pos over {1, 3, 5, 7} (learned workloads)")
     ap.add_argument("--head", default="", help="headline entry mode (default: the fastest learned mode)")
     ap.add_argument("--lanes", type=int, default=3,
                     help="streams that consecutive batches alternate over in the timed steps")
@@ -320,12 +329,27 @@ def build_learned(W, args, torch, ann, synth, dev):
     n, H0, M, dim = spec["n"], spec["hubs"], args.cand, W["dim"]
     times = {}
     t0 = time.time()
-    sample = synth.sample_rows(n, min(n, 262_144), seed=synth.SEED_BASE + 10)
-    init = synth.kmeans_init(len(sample), H0, seed=synth.SEED_BASE + 11)
-    cent = torch.empty((H0, dim), dtype=torch.float32, device=dev)
-    obj = ann.ann_kmeans(W["base"], n, dim, ann.F32, sample, H0, init, 25, cent)
     hubs = torch.empty(H0, dtype=torch.int32, device=dev)
-    ann.ann_assign_hubs(W["base"], n, dim, ann.F32, cent, H0, hubs)
+    if args.hbkm:
+        # hierarchical balanced k-means over every row (Algorithm 2)
+        k, levels = hbkm_shape(H0)
+        keys = torch.from_numpy(synth.hbkm_keys(n, seed=synth.SEED_BASE + 13).view(np.int32)).to(dev)
+        lab = torch.empty(n, dtype=torch.int32, device=dev)
+        ann.ann_hbkm(W["base"], n, dim, k, levels, args.hbkm_lambda, args.hbkm_T, keys, hubs, None, lab)
+        sz = np.bincount(lab.cpu().numpy(), minlength=H0)
+        clustering = dict(method="hbkm", k=k, levels=levels, lam=args.hbkm_lambda, T=args.hbkm_T,
+                          size_min=int(sz.min()), size_max=int(sz.max()), size_std=float(sz.std()))
+    else:
+        # flat Lloyd's k-means on a sample, then the node nearest each centroid
+        sample = synth.sample_rows(n, min(n, 262_144), seed=synth.SEED_BASE + 10)
+        init = synth.kmeans_init(len(sample), H0, seed=synth.SEED_BASE + 11)
+        cent = torch.empty((H0, dim), dtype=torch.float32, device=dev)
+        obj = ann.ann_kmeans(W["base"], n, dim, ann.F32, sample, H0, init, 25, cent)
+        lab = torch.empty(n, dtype=torch.int32, device=dev)
+        ann.ann_assign_hubs(W["base"], n, dim, ann.F32, cent, H0, hubs, lab)
+        sz = np.bincount(lab.cpu().numpy(), minlength=H0)
+        clustering = dict(method="kmeans", objective=[float(obj[0]), float(obj[-1])], size_min=int(sz.min()),
+                          size_max=int(sz.max()), size_std=float(sz.std()))
     hub_np = hubs.cpu().numpy()
     hub_np = hub_np[hub_np >= 0]
     H = len(hub_np)
@@ -345,35 +369,79 @@ def build_learned(W, args, torch, ann, synth, dev):
     ev = torch.empty((nt, M), dtype=torch.int32, device=dev)
     hp = torch.empty_like(ev)
     ann.ann_hub_costs(W["h"], tq, nt, tgt, cand, M, hub_nodes, 64, ev, hp)
+    reached = (hp.cpu().numpy() < 2**31 - 1).mean()
+    times["labels_s"] = time.time() - t0
+    ctx = dict(tq=tq, ev=ev, hp=hp, cand=cand, hub_np=hub_np, hub_nodes=hub_nodes, hub_vecs=hub_vecs, H=H)
+    if args.fusion:
+        # per-hop topology tokens of the hubs' guided subgraph walks (h = 5, Sec. 5.1)
+        t0 = time.time()
+        tok = torch.empty((H, FUSION_HOPS + 1, 8), dtype=torch.float32, device=dev)
+        nodes = torch.empty(H, dtype=torch.int32, device=dev)
+        ann.ann_topo_tokens(W["h"], hub_nodes, H, FUSION_HOPS, tok, nodes)
+        ctx["tokens"] = tok
+        nn = nodes.cpu().numpy()
+        times["tokens_s"] = time.time() - t0
+        ctx["subgraph_nodes"] = dict(mean=float(nn.mean()), min=int(nn.min()), max=int(nn.max()))
+    W["label_ctx"] = ctx
+    out = train_entry_model(W, args, torch, ann, synth, dev, ctx, t_pos=3)
+    times.update(out.pop("times"))
+    return dict(H=H, clustering=clustering, label_reached=float(reached), **out, times=times,
+                fusion=dict(hops=FUSION_HOPS, heads=FUSION_HEADS, head_dim=FUSION_DK,
+                            subgraph_nodes=ctx["subgraph_nodes"]) if args.fusion else None)
+
+
+def hbkm_shape(H):
+    """(k, levels) with k^levels = H and the largest branching k <= 32."""
+    for k in range(32, 1, -1):
+        levels, p = 0, 1
+        while p < H:
+            p *= k
+            levels += 1
+        if p == H:
+            return k, levels
+    raise SystemExit(f"--hbkm: {H} hubs is no power of a branching factor 2..32")
+
+
+def train_entry_model(W, args, torch, ann, synth, dev, ctx, t_pos=3, t_neg=15):
+    """Label rule (Sec. 4.3: hubs within t_pos of the cheapest are positives,
+    beyond t_neg negatives) on the stored label-search costs, then the
+    contrastive training of the two-tower model from its seeded start, and
+    the trained model attached to the index."""
+    times = {}
+    t0 = time.time()
+    tq, H, M, dim = ctx["tq"], ctx["H"], args.cand, W["dim"]
+    nt = tq.shape[0]
     mask = torch.empty((nt, H), dtype=torch.int8, device=dev)
     best = torch.empty(nt, dtype=torch.int32, device=dev)
-    ann.ann_hub_labels(ev, hp, cand, nt, M, H, 3, 15, mask, best)
+    ann.ann_hub_labels(ctx["ev"], ctx["hp"], ctx["cand"], nt, M, H, t_pos, t_neg, mask, best)
     if ann.ann_sync_status(W["h"]) != ann.OK:
         raise RuntimeError("label search reported a device error")
     m = mask.cpu().numpy()
-    reached = (hp.cpu().numpy() < 2**31 - 1).mean()
-    times["labels_s"] = time.time() - t0
+    times["label_rule_s"] = time.time() - t0
 
     t0 = time.time()
     W1, b1, W2, b2, E = synth.model_init(dim, H)
     # hub tower starts at the query tower applied to each hub's own vector
-    ann.ann_set_entry_model(W["h"], dim, W1, b1, W2, b2, hub_np, E, 16)
+    ann.ann_set_entry_model(W["h"], dim, W1, b1, W2, b2, ctx["hub_np"], E, 16)
     E0 = torch.empty((H, 64), dtype=torch.float32, device=dev)
     tmp = torch.empty(H, dtype=torch.int32, device=dev)
-    ann.ann_select_entry(W["h"], hub_vecs, H, ann.ENTRY_LEARNED_EXHAUSTIVE, args.l_hub, tmp, E0)
+    ann.ann_select_entry(W["h"], ctx["hub_vecs"], H, ann.ENTRY_LEARNED_EXHAUSTIVE, args.l_hub, tmp, E0)
     batch = 8192
     t = ann.ann_trainer_create(dim, W1, b1, W2, b2, E0, batch, tau=args.tau, lr=args.lr)
+    if "tokens" in ctx:
+        WQ, WK, WV, WO = synth.fusion_init(dim, 8, FUSION_HEADS, FUSION_DK)
+        ann.ann_trainer_set_fusion(t, ctx["hub_vecs"], ctx["tokens"], FUSION_HOPS + 1, 8, FUSION_HEADS, FUSION_DK,
+                                   WQ, WK, WV, WO)
     order = torch.from_numpy(np.concatenate(
         synth.train_batches(nt, batch, args.epochs, seed=synth.SEED_BASE + 12))).to(dev)
     spe = (nt + batch - 1) // batch
     losses = torch.zeros(max(1, args.epochs * spe), device=dev)
     ann.ann_trainer_fit(t, tq, nt, mask, order, args.epochs, losses)
-    ann.ann_trainer_attach(t, W["h"], hub_nodes, 16)
+    ann.ann_trainer_attach(t, W["h"], ctx["hub_nodes"], 16)
     ann.ann_trainer_free(t)
     ls = losses.cpu().numpy()
     times["train_s"] = time.time() - t0
-    return dict(H=H, kmeans_obj=[float(obj[0]), float(obj[-1])], label_reached=float(reached),
-                positives_per_query=float((m > 0).sum(1).mean()),
+    return dict(t_pos=t_pos, t_neg=t_neg, positives_per_query=float((m > 0).sum(1).mean()),
                 negatives_per_query=float((m < 0).sum(1).mean()),
                 loss_first=float(ls[:spe].mean()), loss_last=float(ls[-spe:].mean()),
                 epochs=args.epochs, lr=args.lr, tau=args.tau, batch=batch, times=times)
@@ -706,6 +774,24 @@ def precision_report(W, torch, ann, args, dev):
     return out
 
 
+def tpos_report(W, torch, ann, synth, args, dev):
+    """The positive threshold t_pos of the label rule swept over {1, 3, 5, 7}
+    (t_neg = 15): relabel from the stored label-search costs, retrain the
+    entry model from the same start, and measure the exhaustive learned
+    entry at its own L* for recall@10 0.95 (the last model stays attached)."""
+    out = {}
+    for tp in (1, 3, 5, 7):
+        info = train_entry_model(W, args, torch, ann, synth, dev, W["label_ctx"], t_pos=tp)
+        r = measure_mode(Runner(W, torch, ann, args, "exhaustive"), torch, ann, W, args, [0.95])
+        tm, _, _ = timed(r["run"], torch, ann, argparse.Namespace(warmup=3, steps=50), r["L"], 1, dev,
+                         lanes=args.lanes)
+        out[str(tp)] = dict(L=r["L"], recall=r["recall"], evals_per_query=r["evals"],
+                            hops_per_query=r["hops"], qps=r["run"].nq * 50 / (tm / 1e3),
+                            positives_per_query=info["positives_per_query"],
+                            loss_first=info["loss_first"], loss_last=info["loss_last"])
+    return out
+
+
 def batch_report(W, torch, ann, args, dev, modes):
     """Per entry mode: mixed per-query k and L in one persistent launch over
     the whole stream (QPS including entry selection, recall@k_i), then
@@ -813,8 +899,8 @@ def run_gpu(args):
     targets = spec["targets"]
 
     res = {}
-    for mode in (["medoid", "learned", "exhaustive", "exhaustive_s2", "exhaustive_s4"] if spec["learned"]
-                 else ["medoid"]):
+    for mode in (["medoid", "learned", "exhaustive", "exhaustive_s2", "exhaustive_s4", "exhaustive_s8"]
+                 if spec["learned"] else ["medoid"]):
         res[mode] = measure_mode(Runner(W, torch, ann, args, mode), torch, ann, W, args, targets)
     # a short timing of every mode picks the headline: the faster learned mode
     # (hub-graph search or exhaustive tensor-core hub scoring), medoid without
@@ -847,6 +933,7 @@ def run_gpu(args):
     prec = precision_report(W, torch, ann, args, dev) if spec.get("precision") else None
     batching = batch_report(W, torch, ann, args, dev, ["medoid"] + ([head] if head != "medoid" else [])) \
         if spec.get("batching") else None
+    tpos = tpos_report(W, torch, ann, synth, args, dev) if args.tpos_sweep and spec["learned"] else None
     peak, peak_kind = peaks()
     n_lanes = len(R["run"].lanes(args.lanes))
     # one lane: a search launch's own event span; several: consecutive
@@ -874,7 +961,8 @@ def run_gpu(args):
                "l2": "inputs larger than L2 (129 MB), no flush" if big
                else "base smaller than L2: an L2-resident parity config",
                "graph_build_s": W["t_build"], "repairs": W["repairs"], "learned": learned,
-               "precision": prec, "batching": batching, "parallelism": f"replicas{world}"}
+               "precision": prec, "batching": batching, "tpos_sweep": tpos,
+               "parallelism": f"replicas{world}"}
         if "medoid" in others:
             med = others["medoid"]
             cfg["learned_vs_medoid"] = {

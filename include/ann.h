@@ -370,7 +370,7 @@ ann_status ann_select_entry(ann_index *idx, const void *d_queries, int64_t nq, i
  *              ann_search_batch with ann_search_params.n_entries = m_seeds
  *   other arguments as for ann_select_entry, which is the m_seeds = 1 case.
  */
-#define ANN_MAX_ENTRY_HUBS 4
+#define ANN_MAX_ENTRY_HUBS 8
 ann_status ann_select_entries(ann_index *idx, const void *d_queries, int64_t nq, int32_t mode, int32_t L_hub,
                               int32_t m_seeds, int32_t *d_entry, float *d_qhat, void *stream);
 
@@ -440,9 +440,34 @@ ann_status ann_trainer_step(ann_trainer *t, const float *d_queries, const int32_
 ann_status ann_trainer_fit(ann_trainer *t, const float *d_queries, int64_t nt, const int8_t *d_mask,
                            const int32_t *d_order, int32_t epochs, float *d_losses, void *stream);
 
-/* Copy the current parameters (gradients != 0: the last step's gradients). */
+/*
+ * Copy the current parameters (gradients != 0: the last step's gradients).
+ * With a fusion tower, hub_emb receives the rows the model scores, E + F,
+ * and its gradient is that of E + F (the same as E's).
+ */
 ann_status ann_trainer_get(const ann_trainer *t, float *W1, float *b1, float *W2, float *b2, float *hub_emb,
                            int32_t gradients);
+
+/*
+ * Topology-aware hub tower (Sec. 4.3, Module I, Eq. fusion): from now on the
+ * hub row of hub v is E_v + F_v with
+ *     F_v = Concat_j softmax((p_v WQ_j)(U_v WK_j)^T / sqrt(head_dim)) (U_v WV_j)  WO
+ * for j = 1..heads, p_v the hub's vector and U_v its T tokens of token_dim
+ * (see ann_topo_tokens), trained with the rest by the same Adam.
+ *   d_hub_vecs  H x in_dim fp32 (device), copied
+ *   d_tokens    H x T x token_dim fp32 (device), copied
+ *   WQ  in_dim x (heads*head_dim); WK, WV  token_dim x (heads*head_dim);
+ *   WO  (heads*head_dim) x 64: initial weights (host or device), copied
+ * Call before the first step; once per trainer.  Blocking.
+ * Errors: ANN_ERR_INVALID_ARG (NULL, sizes, a second call or a call after
+ * a step), ANN_ERR_OOM.
+ */
+ann_status ann_trainer_set_fusion(ann_trainer *t, const float *d_hub_vecs, const float *d_tokens, int32_t T,
+                                  int32_t token_dim, int32_t heads, int32_t head_dim, const float *WQ, const float *WK,
+                                  const float *WV, const float *WO);
+
+/* The fusion weights (gradients != 0: the last step's gradients), as laid out for ann_trainer_set_fusion. */
+ann_status ann_trainer_get_fusion(const ann_trainer *t, float *WQ, float *WK, float *WV, float *WO, int32_t gradients);
 
 /* Attach the trained model to an index (see ann_set_entry_model). */
 ann_status ann_trainer_attach(const ann_trainer *t, ann_index *idx, const int32_t *hub_nodes,
@@ -472,6 +497,66 @@ ann_status ann_adam_update(float *d_params, const float *d_grads, float *d_m, fl
 ann_status ann_kmeans(const void *d_x, int64_t n, int32_t dim, int32_t dtype, const int64_t *sample_rows,
                       int64_t m, int32_t k, const int32_t *init, int32_t iters, float *d_centroids,
                       double *objective, void *stream);
+
+/*
+ * Per-hop topology tokens of hub nodes (Sec. 4.2, subgraph sampling; a fixed
+ * summary in place of Graph2Vec), for the fusion tower.  The guided walk from
+ * each hub: MinDeg / MaxDeg are the smallest / largest valid-neighbour counts
+ * in the graph; a FIFO queue starts at the hub (hop 0); a dequeued node u at
+ * hop < h ranks its deg(u) valid neighbours by (squared L2 to u, id) and
+ * samples the ceil(x/2) nearest and floor(x/2) farthest,
+ * x = ceil(MinDeg * deg(u) / MaxDeg); a sampled neighbour not yet in the
+ * subgraph joins at hop(u)+1 with parent u, in rank order, until max_nodes.
+ * Token l = 0..h of a hub (8 floats), s = the hub's mean squared distance to
+ * its valid neighbours (1 if none or 0): hop-l nodes / all nodes, their mean
+ * degree / MaxDeg, mean and max squared distance to the hub / s, mean squared
+ * distance to the parent / s, share sampled as farthest, l / h, 1 (the first
+ * six 0 for an empty hop).  float32, each operation rounded on its own,
+ * coordinates summed in order and a hop's nodes in joining order.
+ *   d_hubs     H node ids (device), checked against n
+ *   d_tokens   out: H x (h+1) x 8 fp32
+ *   d_nodes    out (optional): H subgraph sizes
+ * Needs fp32 rows (an ANN_F32 index, or base_f32 given at creation), degree
+ * <= 64 and dim % 4 == 0 (else ANN_ERR_UNSUPPORTED); 1 <= h <= 64,
+ * 1 <= max_nodes <= 8192.  Blocking.
+ */
+ann_status ann_topo_tokens(ann_index *idx, const int32_t *d_hubs, int32_t H, int32_t h, int32_t max_nodes,
+                           float *d_tokens, int32_t *d_nodes, void *stream);
+
+/*
+ * Hierarchical balanced k-means, HBKM (Sec. 4.1, Def. 2 and Algorithm 2), with
+ * the hub of every final cluster (Def. 3).  `levels` rounds each split every
+ * cluster of the round before (round 0: all n rows) into k children, so
+ * k^levels clusters come out; child j of cluster c is cluster c*k + j.  A
+ * split runs T iterations; each empties the children, visits the cluster's
+ * members in increasing row id and puts row x into
+ *     argmin_j ||x - mu_j||^2 + lam * (2 (c_j - m) + 1)   (ties: smaller j)
+ * with c_j child j's current size, m = |C|/k, lam = lambda * sigma^2 / m and
+ * sigma^2 the members' mean squared distance to C's centroid (the penalty is
+ * the increase of Def. 2's size variance sum (|C_j| - m)^2 that the move
+ * causes); then every non-empty child moves to its members' mean and an empty
+ * one keeps its centroid.  A split starts at its members with the
+ * min(k, |C|) smallest (d_keys[id], id), in that order; children beyond |C|
+ * stay empty at C's centroid.  All arithmetic is float32 with each operation
+ * rounded on its own, distances summed over coordinates 0..dim-1 and sigma^2
+ * and means over members in increasing id, so results are reproducible bit
+ * for bit.
+ *   d_x          n x dim fp32 rows (device, 16-byte aligned), dim % 4 == 0,
+ *                4 <= dim <= 4096, 1 <= n < 2^31
+ *   k, levels    2 <= k <= 32, levels >= 1, k^levels <= 2^20
+ *   lambda       penalty strength >= 0 (0: plain k-means splits)
+ *   T            iterations per split, >= 1
+ *   d_keys       n uint32 (device): the draw that picks the starting members
+ *   d_hubs       out: k^levels int32 row ids, the member nearest each final
+ *                centroid (smaller id on ties), -1 for an empty cluster
+ *   d_centroids  out (optional): k^levels x dim fp32 final centroids
+ *   d_label      out (optional): n int32 final cluster of every row
+ * Blocking.  Errors: ANN_ERR_INVALID_ARG for a NULL input or output, bad
+ * sizes or alignment; ANN_ERR_UNSUPPORTED when k x dim floats do not fit in
+ * one block's shared memory.
+ */
+ann_status ann_hbkm(const float *d_x, int64_t n, int32_t dim, int32_t k, int32_t levels, double lambda, int32_t T,
+                    const uint32_t *d_keys, int32_t *d_hubs, float *d_centroids, int32_t *d_label, void *stream);
 
 /*
  * Hub nodes (Sec. 4.1, Def. 3): assign every base row to its nearest centroid;

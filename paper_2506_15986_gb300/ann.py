@@ -20,7 +20,7 @@ OK, ERR_INVALID_ARG, ERR_IO, ERR_FORMAT, ERR_OOM, ERR_CUDA, ERR_CAPACITY, ERR_TI
 U8, F32, F16, BF16, I8S = 0, 1, 2, 3, 4
 L2, IP = 0, 1
 SEARCH_RERANK, SEARCH_FAULT_WAIT = 1, 2
-MAX_L, MAX_W, MAX_STEP_CAND, MAX_SEEDS, MAX_ENTRY_HUBS = 2048, 4, 128, 32, 4
+MAX_L, MAX_W, MAX_STEP_CAND, MAX_SEEDS, MAX_ENTRY_HUBS = 2048, 4, 128, 32, 8
 
 _c = ctypes
 _p = ctypes.c_void_p
@@ -100,6 +100,10 @@ def load_library(path: str | None = None):
                              _c.c_float, _p], i32),
         "ann_kmeans": ([_p, i64, i32, i32, _p, i64, i32, _p, i32, _p, _p, _p], i32),
         "ann_assign_hubs": ([_p, i64, i32, i32, _p, i32, _p, _p, _p], i32),
+        "ann_hbkm": ([_p, i64, i32, i32, i32, _c.c_double, i32, _p, _p, _p, _p, _p], i32),
+        "ann_topo_tokens": ([_p, _p, i32, i32, i32, _p, _p, _p], i32),
+        "ann_trainer_set_fusion": ([_p, _p, _p, i32, i32, i32, i32, _p, _p, _p, _p], i32),
+        "ann_trainer_get_fusion": ([_p, _p, _p, _p, _p, i32], i32),
         "ann_hub_costs": ([_p, _p, i64, _p, _p, i32, _p, i32, i32, _p, _p, _p], i32),
         "ann_hub_labels": ([_p, _p, _p, i64, i32, i32, i32, i32, _p, _p, _p], i32),
     }
@@ -416,3 +420,30 @@ def ann_select_entry_noalloc_max_queries():
     lib.ann_select_entry_noalloc_max_queries.argtypes = []
     lib.ann_select_entry_noalloc_max_queries.restype = _c.c_int64
     return int(lib.ann_select_entry_noalloc_max_queries())
+
+
+def ann_hbkm(x, n, dim, k, levels, lam, T, keys, hubs_out, centroids_out=None, label_out=None, stream=None):
+    """Hierarchical balanced k-means and its hubs (device buffers); blocking."""
+    _check(load_library().ann_hbkm(_ptr(x), int(n), int(dim), int(k), int(levels), float(lam), int(T),
+                                   _ptr(keys), _ptr(hubs_out), _ptr(centroids_out), _ptr(label_out),
+                                   _stream(stream)), "ann_hbkm")
+
+
+def ann_topo_tokens(h, hubs, H, hops, tokens_out, nodes_out=None, max_nodes=4096, stream=None):
+    """Per-hop topology tokens of H hubs (device buffers); blocking."""
+    _check(load_library().ann_topo_tokens(h, _ptr(hubs), int(H), int(hops), int(max_nodes), _ptr(tokens_out),
+                                          _ptr(nodes_out), _stream(stream)), "ann_topo_tokens")
+
+
+def ann_trainer_set_fusion(t, hub_vecs, tokens, T, token_dim, heads, head_dim, WQ, WK, WV, WO):
+    """Give the trainer the topology-aware hub tower (weights: numpy or device)."""
+    import numpy as np
+    keep = [np.ascontiguousarray(w, np.float32) if isinstance(w, np.ndarray) else w for w in (WQ, WK, WV, WO)]
+    _check(load_library().ann_trainer_set_fusion(t, _ptr(hub_vecs), _ptr(tokens), int(T), int(token_dim),
+                                                 int(heads), int(head_dim), *[_ptr(w) for w in keep]),
+           "ann_trainer_set_fusion")
+
+
+def ann_trainer_get_fusion(t, WQ=None, WK=None, WV=None, WO=None, gradients=False):
+    _check(load_library().ann_trainer_get_fusion(t, _ptr(WQ), _ptr(WK), _ptr(WV), _ptr(WO), int(bool(gradients))),
+           "ann_trainer_get_fusion")

@@ -461,6 +461,10 @@ ann_status launch_hub_argmax(const ann_entry_model *m, const Operand &Q, int64_t
     case 2: return launch_hub_topm<2>(m, Q, nq, out_node, out_hub, out_score, status, s);
     case 3: return launch_hub_topm<3>(m, Q, nq, out_node, out_hub, out_score, status, s);
     case 4: return launch_hub_topm<4>(m, Q, nq, out_node, out_hub, out_score, status, s);
+    case 5: return launch_hub_topm<5>(m, Q, nq, out_node, out_hub, out_score, status, s);
+    case 6: return launch_hub_topm<6>(m, Q, nq, out_node, out_hub, out_score, status, s);
+    case 7: return launch_hub_topm<7>(m, Q, nq, out_node, out_hub, out_score, status, s);
+    case 8: return launch_hub_topm<8>(m, Q, nq, out_node, out_hub, out_score, status, s);
     default: return ANN_ERR_INVALID_ARG;
     }
 }

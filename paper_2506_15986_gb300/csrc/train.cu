@@ -26,6 +26,7 @@
 #include <vector>
 
 #include "entry.h"
+#include "fusion.h"
 #include "internal.h"
 #include "tc.cuh"
 
@@ -302,6 +303,7 @@ struct ann_trainer {
     __nv_bfloat16 *a1 = nullptr, *qbf = nullptr, *EnT = nullptr, *dST = nullptr, *qT = nullptr, *a1T = nullptr,
                   *dZ2T = nullptr, *xT = nullptr, *dZ1T = nullptr;
     std::vector<void *> owned;
+    ann::Fusion *fu = nullptr;  // topology-aware hub tower: hub rows are E + F
 };
 
 namespace {
@@ -325,7 +327,22 @@ void trainer_free(ann_trainer *t)
     cudaDeviceSynchronize();
     for (void *p : t->owned)
         cudaFree(p);
+    fusion_free(t->fu);
     delete t;
+}
+
+// one Adam step over every parameter block
+void adam_all(ann_trainer *t, cudaStream_t s)
+{
+    t->step += 1;
+    const float bc1 = 1.f - powf(t->beta1, static_cast<float>(t->step));
+    const float bc2 = 1.f - powf(t->beta2, static_cast<float>(t->step));
+    adam_kernel<<<blocks_for(t->n_params, 256), 256, 0, s>>>(t->params, t->grads, t->m, t->v, t->n_params, t->lr,
+                                                             t->beta1, t->beta2, t->eps, bc1, bc2);
+    if (t->fu)
+        adam_kernel<<<blocks_for(t->fu->n_params, 256), 256, 0, s>>>(t->fu->params, t->fu->grads, t->fu->m,
+                                                                     t->fu->v, t->fu->n_params, t->lr, t->beta1,
+                                                                     t->beta2, t->eps, bc1, bc2);
 }
 
 // offsets of the parameter blocks inside the flat vector
@@ -351,10 +368,19 @@ ann_status trainer_grads(ann_trainer *t, const float *d_queries, const int32_t *
     ann_entry_model &M = t->model;
     const Offs o = offsets(t->in_dim, t->H);
     const int H = t->H, D = t->in_dim;
-    ann_status st = prepare_model(&M, s);
+    ann_status st = ANN_OK;
+    if (t->fu) {
+        // the hub rows the model scores: E + F (Eq. fusion)
+        if ((st = fusion_forward(t->fu, t->params + o.E, s)) != ANN_OK)
+            return st;
+        M.E = t->fu->Eeff;
+    }
+    st = prepare_model(&M, s);
+    M.E = t->params + o.E;
     if (st != ANN_OK)
         return st;
-    row_norms_kernel<<<blocks_for(H, 256), 256, 0, s>>>(M.E, H, 64, t->Enrm);
+    const float *Erows = t->fu ? t->fu->Eeff : M.E;
+    row_norms_kernel<<<blocks_for(H, 256), 256, 0, s>>>(Erows, H, 64, t->Enrm);
     const Operand X{d_queries, OP_F32, D, 1, B, D, rows};
     st = launch_tower(&M, X, B, t->qhat, t->qbf, t->z1, t->a1, t->nrm, t->status, s);
     if (st != ANN_OK)
@@ -407,6 +433,9 @@ ann_status trainer_grads(ann_trainer *t, const float *d_queries, const int32_t *
     norm_backward_kernel<<<blocks_for(B * 32, 256), 256, 0, s>>>(t->qhat, t->nrm, t->dQ, B, 64, t->dZ2);
     norm_backward_kernel<<<blocks_for(static_cast<int64_t>(H) * 32, 256), 256, 0, s>>>(M.En, t->Enrm, t->dEh, H, 64,
                                                                                       t->grads + o.E);
+    // dL/dF = dL/d(E + F) = dL/dE
+    if (t->fu && (st = fusion_backward(t->fu, t->grads + o.E, s)) != ANN_OK)
+        return st;
     // dW2 = A1^T dZ2 (256 x 64, K = B); db2
     transpose_bf16<<<dim3(blocks_for(256, 32), blocks_for(B, 32)), dim3(32, 8), 0, s>>>(
         Operand{t->a1, OP_BF16, 256, 1, B, 256, nullptr}, B, 256, t->a1T);
@@ -575,11 +604,7 @@ ann_status ann_trainer_step(ann_trainer *t, const float *d_queries, const int32_
     if (st != ANN_OK)
         return st;
     if (apply_update) {
-        t->step += 1;
-        const float bc1 = 1.f - powf(t->beta1, static_cast<float>(t->step));
-        const float bc2 = 1.f - powf(t->beta2, static_cast<float>(t->step));
-        adam_kernel<<<blocks_for(t->n_params, 256), 256, 0, s>>>(t->params, t->grads, t->m, t->v, t->n_params,
-                                                                 t->lr, t->beta1, t->beta2, t->eps, bc1, bc2);
+        adam_all(t, s);
         st = cuda_status(cudaGetLastError());
     }
     if (st == ANN_OK && loss_out) {
@@ -607,7 +632,15 @@ ann_status ann_trainer_get(const ann_trainer *t, float *W1, float *b1, float *W2
     cp(b1, o.b1, 256);
     cp(W2, o.W2, 256 * 64);
     cp(b2, o.b2, 64);
-    cp(hub_emb, o.E, static_cast<int64_t>(t->H) * 64);
+    if (hub_emb && t->fu && !gradients && e == cudaSuccess) {
+        // the hub rows the model scores: E + F with the current weights
+        ann_status st = fusion_forward(t->fu, t->params + o.E, nullptr);
+        if (st != ANN_OK)
+            return st;
+        e = cudaMemcpy(hub_emb, t->fu->Eeff, static_cast<size_t>(t->H) * 64 * 4, cudaMemcpyDefault);
+    } else {
+        cp(hub_emb, o.E, static_cast<int64_t>(t->H) * 64);
+    }
     if (e == cudaSuccess) {
         int st = 0;
         e = cudaMemcpy(&st, t->status, 4, cudaMemcpyDeviceToHost);
@@ -645,11 +678,7 @@ ann_status ann_trainer_fit(ann_trainer *t, const float *d_queries, int64_t nt, c
             st = trainer_grads(t, d_queries, ord + i * t->batch, nb, d_mask, s);
             if (st != ANN_OK)
                 break;
-            t->step += 1;
-            const float bc1 = 1.f - powf(t->beta1, static_cast<float>(t->step));
-            const float bc2 = 1.f - powf(t->beta2, static_cast<float>(t->step));
-            adam_kernel<<<blocks_for(t->n_params, 256), 256, 0, s>>>(t->params, t->grads, t->m, t->v, t->n_params,
-                                                                     t->lr, t->beta1, t->beta2, t->eps, bc1, bc2);
+            adam_all(t, s);
             if (d_losses)
                 cudaMemcpyAsync(d_losses + ep * spe + i, t->loss, 4, cudaMemcpyDeviceToDevice, s);
             st = cuda_status(cudaGetLastError());
@@ -681,10 +710,49 @@ ann_status ann_trainer_attach(const ann_trainer *t, ann_index *idx, const int32_
     d.n_hubs = t->H;
     d.hub_nodes = hub_nodes;
     d.hub_emb = t->model.E;
+    if (t->fu) {
+        ann_status st = fusion_forward(t->fu, t->model.E, nullptr);
+        if (st == ANN_OK)
+            st = cuda_status(cudaDeviceSynchronize());
+        if (st != ANN_OK)
+            return st;
+        d.hub_emb = t->fu->Eeff;
+    }
     d.hub_degree = hub_degree;
     d.hub_graph = nullptr;
     d.hub_entry = -1;
     return ann_set_entry_model(idx, &d, stream);
+}
+
+ann_status ann_trainer_set_fusion(ann_trainer *t, const float *d_hub_vecs, const float *d_tokens, int32_t T,
+                                  int32_t token_dim, int32_t heads, int32_t head_dim, const float *WQ, const float *WK,
+                                  const float *WV, const float *WO)
+{
+    if (!t || !d_hub_vecs || !d_tokens || !WQ || !WK || !WV || !WO || t->fu || t->step != 0 || T < 1 || T > 64 ||
+        token_dim < 1 || token_dim > 64 || heads < 1 || head_dim < 1 || heads * head_dim > 256)
+        return ANN_ERR_INVALID_ARG;
+    cudaSetDevice(t->device);
+    cudaError_t e = cudaSuccess;
+    t->fu = fusion_create(t->H, T, token_dim, heads, head_dim, t->in_dim, d_hub_vecs, d_tokens, WQ, WK, WV, WO, e);
+    return cuda_status(e);
+}
+
+ann_status ann_trainer_get_fusion(const ann_trainer *t, float *WQ, float *WK, float *WV, float *WO, int32_t gradients)
+{
+    if (!t || !t->fu)
+        return ANN_ERR_INVALID_ARG;
+    const Fusion *f = t->fu;
+    const float *src = gradients ? f->grads : f->params;
+    cudaError_t e = cudaDeviceSynchronize();
+    auto cp = [&](float *dst, int64_t off, int64_t count) {
+        if (dst && e == cudaSuccess)
+            e = cudaMemcpy(dst, src + off, count * 4, cudaMemcpyDefault);
+    };
+    cp(WQ, f->oWQ(), static_cast<int64_t>(f->dp) * f->E);
+    cp(WK, f->oWK(), static_cast<int64_t>(f->dU) * f->E);
+    cp(WV, f->oWV(), static_cast<int64_t>(f->dU) * f->E);
+    cp(WO, f->oWO(), static_cast<int64_t>(f->E) * f->dF);
+    return cuda_status(e);
 }
 
 ann_status ann_adam_update(float *d_params, const float *d_grads, float *d_m, float *d_v, int64_t n, int64_t step,

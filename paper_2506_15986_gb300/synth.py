@@ -196,6 +196,19 @@ def kmeans_init(m, k, seed):
     return _rng(seed).permutation(m)[:k].astype(np.int32)
 
 
+def fusion_init(dp, dU, heads, dk, out=64, seed=SEED_BASE + 101):
+    """Initial fusion-attention weights (Eq. fusion): WQ [dp, heads*dk],
+    WK and WV [dU, heads*dk], WO [heads*dk, out], Glorot-scaled normal draws;
+    WO starts small so that the hub rows start near the free embeddings."""
+    rng = _rng(seed)
+    E = heads * dk
+    WQ = rng.standard_normal((dp, E)) / np.sqrt(dp)
+    WK = rng.standard_normal((dU, E)) / np.sqrt(dU)
+    WV = rng.standard_normal((dU, E)) / np.sqrt(dU)
+    WO = 0.1 * rng.standard_normal((E, out)) / np.sqrt(E)
+    return tuple(w.astype(np.float32) for w in (WQ, WK, WV, WO))
+
+
 def hbkm_keys(n, seed):
     """One uniform uint32 key per row: the draw from which hierarchical
     balanced k-means takes each split's initial centroids (the members with

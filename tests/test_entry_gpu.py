@@ -184,7 +184,7 @@ def _select_m(s, mode, m, L_hub=32):
     return ent.cpu().numpy()
 
 
-@pytest.mark.parametrize("m", [1, 2, 4])
+@pytest.mark.parametrize("m", [1, 2, 4, 5, 8])
 def test_exhaustive_top_m_hubs(setup, m):
     # the m best hubs by the scores the tensor cores see, best first; one
     # seed is exactly the single-entry selection
@@ -219,3 +219,15 @@ def test_seed_sets_drive_search(setup):
     assert st == ann.OK and (ids == oi).mean() >= 0.999
     ok = ids == oi
     assert (np.abs(d - od)[ok] / np.maximum(od[ok], 1e-30)).max() <= 1e-5
+
+
+def test_seed_count_limits(setup):
+    nq = 4
+    dq = torch.from_numpy(setup["q"][:nq]).to(DEV)
+    ent = torch.empty((nq, 9), dtype=torch.int32, device=DEV)
+    for m in (0, ann.MAX_ENTRY_HUBS + 1):
+        with pytest.raises(ann.AnnError) as e:
+            ann.ann_select_entries(setup["h"], dq, nq, ann.ENTRY_LEARNED_EXHAUSTIVE, 32, m, ent)
+        assert e.value.status == ann.ERR_INVALID_ARG
+    with pytest.raises(ann.AnnError):  # the hub-graph pool must hold m hubs
+        ann.ann_select_entries(setup["h"], dq, nq, ann.ENTRY_LEARNED_NAV, 4, 8, ent)
