@@ -990,7 +990,7 @@ def run_gpu(args):
                          "launch_ms_basis": "event span of one launch" if n_lanes == 1
                          else f"timed region / steps, {n_lanes} lanes overlapping",
                          "launch_span_ms": search_ms,
-                         "isolated_launch_ms": (R["tune"] or {}).get("search_ms")},
+                         "autotune_ms_per_batch": (R["tune"] or {}).get("search_ms")},
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": args.steps * R["run"].launches(),
         }
