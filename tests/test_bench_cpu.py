@@ -1,0 +1,51 @@
+"""Host logic of bench.py that needs no GPU: the hub-count factorisation for
+hierarchical balanced k-means, the kernel-source digest's insensitivity to
+comments and prototypes, and the mode names."""
+import os
+import shutil
+
+import pytest
+
+import bench
+
+
+def test_hbkm_shape():
+    assert bench.hbkm_shape(1024) == (32, 2)
+    assert bench.hbkm_shape(4096) == (16, 3)
+    assert bench.hbkm_shape(16384) == (4, 7)
+    assert bench.hbkm_shape(27) == (27, 1)
+    for H in (1024, 4096, 16384, 27, 512):
+        k, levels = bench.hbkm_shape(H)
+        assert k ** levels == H and 2 <= k <= 32
+    assert bench.hbkm_shape(1000) == (10, 3)
+    with pytest.raises(SystemExit):
+        bench.hbkm_shape(1001)  # 7 * 11 * 13: no power of one branching factor
+
+
+def test_kernel_digest_ignores_comments_and_prototypes(tmp_path, monkeypatch):
+    root = tmp_path / "r"
+    for rel in ("paper_2506_15986_gb300/csrc", "include"):
+        (root / rel).mkdir(parents=True)
+    for rel in ("paper_2506_15986_gb300/csrc/search.cu", "paper_2506_15986_gb300/csrc/device_util.cuh",
+                "paper_2506_15986_gb300/csrc/internal.h", "include/ann.h"):
+        shutil.copy(os.path.join(bench.ROOT, rel), root / rel)
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    d0 = bench.kernel_digest()
+    hdr = root / "include/ann.h"
+    text = hdr.read_text()
+    hdr.write_text(text.replace("#endif", "/* a note */\nann_status ann_new_call(ann_index *idx, int32_t x);\n#endif", 1))
+    assert bench.kernel_digest() == d0  # a comment and a new prototype
+    hdr.write_text(text.replace("#define ANN_MAX_L 2048", "#define ANN_MAX_L 4096"))
+    assert bench.kernel_digest() != d0  # a constant the kernel compiles against
+    hdr.write_text(text)
+    cu = root / "paper_2506_15986_gb300/csrc/search.cu"
+    cu.write_text(cu.read_text() + "\n// trailing note\n")
+    assert bench.kernel_digest() == d0
+
+
+def test_mode_names():
+    class A:
+        ENTRY_MEDOID, ENTRY_LEARNED_NAV, ENTRY_LEARNED_EXHAUSTIVE = 0, 1, 2
+    assert bench.mode_info(A, "medoid") == (0, 1)
+    assert bench.mode_info(A, "learned") == (1, 1)
+    assert bench.mode_info(A, "exhaustive_s8") == (2, 8)
