@@ -47,7 +47,18 @@ struct GemmArgs {
     float *out;
     int64_t ldo;
     int *status;
+    int64_t ksplit;         // > 0: blockIdx.z takes K range [z*ksplit, (z+1)*ksplit) and adds into out
 };
+
+// the operand seen from column k0 on (k0 a multiple of 64: 16-byte alignment kept)
+__device__ __forceinline__ Operand op_from_k(const Operand &o, int64_t k0)
+{
+    Operand r = o;
+    const int es = o.type == OP_F32 ? 4 : (o.type == OP_BF16 ? 2 : 1);
+    r.p = static_cast<const uint8_t *>(o.p) + k0 * o.sk * es;
+    r.cols = o.cols - k0;
+    return r;
+}
 
 template <int BN>
 __global__ void __launch_bounds__(128) gemm_kernel(const GemmArgs g)
@@ -73,7 +84,10 @@ __global__ void __launch_bounds__(128) gemm_kernel(const GemmArgs g)
     tc_fence_after();
     const uint32_t tmem = *slot;
     uint32_t phase = 0;
-    const bool ok = tc_gemm_tile<BN>(g.A, r0, g.B, c0, g.K, sA, sB, bar, phase, tmem);
+    const int64_t kb = g.ksplit > 0 ? static_cast<int64_t>(blockIdx.z) * g.ksplit : 0;
+    const int64_t kl = g.ksplit > 0 ? min(g.ksplit, g.K - kb) : g.K;
+    const bool ok = tc_gemm_tile<BN>(kb ? op_from_k(g.A, kb) : g.A, r0, kb ? op_from_k(g.B, kb) : g.B, c0, kl, sA,
+                                     sB, bar, phase, tmem);
     if (ok) {
         const float a = g.alpha * (g.scale ? g.scale[0] : 1.f);
         const uint32_t my_lane = tmem + (static_cast<uint32_t>(warp * 32) << 16);
@@ -88,7 +102,10 @@ __global__ void __launch_bounds__(128) gemm_kernel(const GemmArgs g)
                         float x = a * v[j];
                         if (g.epi == EPI_RELU_MASK && !(g.aux[row * g.ldo + col] > 0.f))
                             x = 0.f;
-                        g.out[row * g.ldo + col] = x;
+                        if (g.ksplit > 0)
+                            atomicAdd(g.out + row * g.ldo + col, x);  // a partial sum over its K range
+                        else
+                            g.out[row * g.ldo + col] = x;
                     }
                 }
             }
@@ -113,7 +130,24 @@ ann_status gemm(const GemmArgs &g, cudaStream_t s)
     if (e != cudaSuccess)
         return cuda_status(e);
     dim3 grid(static_cast<unsigned>((g.M + 127) / 128), static_cast<unsigned>((g.N + BN - 1) / BN));
-    gemm_kernel<BN><<<grid, 128, smem, s>>>(g);
+    // few output tiles over a long reduction: split K over CTAs (linear
+    // epilogue only), at least 512 columns each, up to about two CTAs per SM
+    GemmArgs h = g;
+    h.ksplit = 0;
+    const int64_t tiles = static_cast<int64_t>(grid.x) * grid.y;
+    if (g.epi == EPI_STORE && tiles < 128 && g.K >= 1024) {
+        const int64_t want = std::min<int64_t>(g.K / 512, std::max<int64_t>(1, 256 / tiles));
+        if (want > 1) {
+            h.ksplit = ((g.K + want - 1) / want + 63) / 64 * 64;
+            grid.z = static_cast<unsigned>((g.K + h.ksplit - 1) / h.ksplit);
+            // the partial sums add into a zeroed M x N block (rows ldo apart)
+            e = cudaMemset2DAsync(g.out, static_cast<size_t>(g.ldo) * 4, 0, static_cast<size_t>(g.N) * 4,
+                                  static_cast<size_t>(g.M), s);
+            if (e != cudaSuccess)
+                return cuda_status(e);
+        }
+    }
+    gemm_kernel<BN><<<grid, 128, smem, s>>>(h);
     return cuda_status(cudaGetLastError());
 }
 

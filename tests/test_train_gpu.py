@@ -41,10 +41,13 @@ def _cos(a, b):
     return float((a * b).sum() / (np.linalg.norm(a) * np.linalg.norm(b)))
 
 
-def test_gradients_match_oracle():
-    X, W1, b1, W2, b2, E, mask, rows = _problem()
+@pytest.mark.parametrize("B", [700, 3000])
+def test_gradients_match_oracle(B):
+    # B = 3000: the reductions over the batch (dE, dW1, dW2) are split over
+    # K ranges whose partial sums add into the output, the last range ragged
+    X, W1, b1, W2, b2, E, mask, rows = _problem(B=B)
     tau = 0.1
-    t = ann.ann_trainer_create(128, W1, b1, W2, b2, E, 1024, tau=tau, lr=1e-3)
+    t = ann.ann_trainer_create(128, W1, b1, W2, b2, E, 4096, tau=tau, lr=1e-3)
     try:
         dX = torch.from_numpy(X).to(DEV)
         dm = torch.from_numpy(mask).to(DEV)
