@@ -83,3 +83,60 @@ def test_full_size_sampled_parity(full, seeds):
     assert (np.abs(gd[same] - od[same]) <= 1e-5 * np.maximum(od[same], 1e-30)).all()
     assert abs(_recall(gi, full["gt"][sample]) - _recall(oi, full["gt"][sample])) <= 0.001
     assert (st[sample, 0] == oe).mean() >= 0.99 and (st[sample, 1] == oh).mean() >= 0.99
+
+
+def _other(gen, R, metric, L, W, tuned, nq, seeds):
+    """Build a million-row workload, run its bench configuration on three
+    lanes and compare 100 sampled queries with the oracle."""
+    w = gen()
+    x = w["base"]
+    n, d = x.shape
+    base = torch.from_numpy(x).to(DEV)
+    graph = torch.empty((n, R), dtype=torch.int32, device=DEV)
+    med, _ = ann.ann_build_graph(base, n, d, ann.F32, 64, R, 1.0, graph)
+    qn = w["queries"][:nq]
+    q = torch.from_numpy(np.ascontiguousarray(qn)).to(DEV)
+    h = ann.ann_index_create(base, graph, med, ann.F32, metric)
+    try:
+        rng = np.random.default_rng(5)
+        ent_np = rng.integers(0, n, size=(nq, seeds)).astype(np.int32) if seeds else None
+        ent = None if ent_np is None else torch.from_numpy(ent_np).to(DEV)
+        p = ann.search_params(K, L, W=W, n_entries=seeds, **tuned)
+        outs = []
+        torch.cuda.synchronize()
+        for s in [torch.cuda.Stream(device=DEV) for _ in range(3)]:
+            with torch.cuda.stream(s):
+                ids = torch.empty((nq, K), dtype=torch.int32, device=DEV)
+                dd = torch.empty((nq, K), dtype=torch.float32, device=DEV)
+            ann.ann_search_batch(h, q, nq, ent, p, ids, dd, None, s)
+            outs.append((ids, dd))
+        torch.cuda.synchronize()
+        assert ann.ann_sync_status(h) == ann.OK
+        res = [(a.cpu().numpy(), b.cpu().numpy()) for a, b in outs]
+    finally:
+        ann.ann_free_index(h)
+    for r in res[1:]:
+        assert np.array_equal(r[0], res[0][0]) and np.array_equal(r[1], res[0][1])
+    sample = np.sort(rng.choice(nq, 100, replace=False))
+    e = med if ent_np is None else ent_np[sample]
+    oi, od, _, _ = oracle.search(x, graph.cpu().numpy(), qn[sample].astype(np.float64), e, L, K, W=W,
+                                 metric=oracle.IP if metric == ann.IP else oracle.L2)
+    gi, gd = res[0][0][sample], res[0][1][sample].astype(np.float64)
+    same = gi == oi
+    assert same.mean() >= 0.999, same.mean()
+    scale = np.maximum(np.abs(od[same]), 1e-30) if metric == ann.L2 else \
+        np.linalg.norm(x[gi[same]], axis=1) * np.linalg.norm(qn[sample], axis=1)[np.nonzero(same)[0]]
+    assert (np.abs(gd[same] - od[same]) <= 1e-5 * scale).all()
+
+
+def test_full_size_ip_config():
+    # 1M x 200 unit vectors, maximum inner product, out-of-distribution
+    # queries; L = 1,088 (recall 0.95), the bench's tuned sizes, 2-node seeds
+    _other(lambda: synth.ip_f32(n=1_000_000, nq=10_000, n_train=0), 32, ann.IP, 1088, 4,
+           dict(hash_bits=-1, stage_rows=4, team=8, spill_bits=16), 10_000, 2)
+
+
+def test_full_size_960d_config():
+    # 1M x 960 fp32 (3.84 GB), R = 48, W = 2, L = 224, 1,000 queries, medoid
+    _other(lambda: synth.highdim_f32(n=1_000_000, nq=1_000), 48, ann.L2, 224, 2,
+           dict(hash_bits=-1, stage_rows=4, team=16, spill_bits=16), 1_000, 0)
