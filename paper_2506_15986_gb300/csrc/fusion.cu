@@ -9,6 +9,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <new>
 
 #include "fusion.h"
 
@@ -190,7 +191,11 @@ T *falloc(size_t count, cudaError_t &e)
 Fusion *fusion_create(int H, int T, int dU, int heads, int dk, int dp, const float *P, const float *U,
                       const float *WQ, const float *WK, const float *WV, const float *WO, cudaError_t &e)
 {
-    Fusion *f = new Fusion();
+    Fusion *f = new (std::nothrow) Fusion();
+    if (!f) {
+        e = cudaErrorMemoryAllocation;
+        return nullptr;
+    }
     f->H = H;
     f->T = T;
     f->dU = dU;
