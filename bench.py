@@ -706,7 +706,13 @@ def cpu_baseline(W, L, entries=None, target_s=10.0, width=1, k=K_NN):
         dt = time.perf_counter() - t
         if dt >= 0.5 * target_s or passes >= 50:
             break
+    # one thread, the paper's query regime (one query thread, Sec. 5.1): about 2 s
+    m1 = int(min(len(allq), max(8, 2.0 / max(per_q * oracle.num_threads(), 1e-9))))
+    t1 = time.perf_counter()
+    oracle.search(base, g, allq[:m1], ent[:m1], L, k, W=width, metric=metric, threads=1)
+    qps1 = m1 / (time.perf_counter() - t1)
     return {"value": done / dt, "unit": "queries/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "value_1thread": qps1, "sample_1thread": f"the first {m1} evaluation queries on one thread",
             "sample": f"{passes} pass(es) over the first {m} of the {len(allq)} evaluation queries at "
                       f"L={L}, W={width}, entries as the GPU arm, float64 distances, one query per "
                       f"OpenMP thread ({dt:.1f} s)",
