@@ -60,7 +60,7 @@ sys.path.insert(0, ROOT)
 FUSION_HOPS, FUSION_HEADS, FUSION_DK = 5, 4, 16  # h = 5 as in Sec. 5.1; 4 heads of 16
 METRIC = "QPS at recall@10=0.95 on 1 GB300, learned vs medoid entry; dist evals/query"
 L_SWEEP = [16, 24, 32, 40, 48, 56, 64, 72, 80, 88, 96, 112, 128, 144, 160, 176, 192, 224, 256, 320,
-           384, 448, 512, 640, 768, 1024, 1536, 2048]
+           384, 448, 512, 640, 768, 1024, 1536, 2048, 3072, 4096]
 K_NN = 10
 
 WORKLOADS = {

@@ -62,7 +62,7 @@ typedef struct ann_index ann_index;
 #define ANN_SEARCH_FAULT_WAIT 2u /* fault injection for tests of the timeout path (see ann_search_params) */
 
 /* Limits of one search */
-#define ANN_MAX_L 2048     /* pool size L */
+#define ANN_MAX_L 4096     /* pool size L */
 #define ANN_MAX_W 4        /* entries expanded per step */
 #define ANN_MAX_STEP_CAND 128 /* W * degree */
 #define ANN_MAX_SEEDS 32   /* seed nodes per query (n_entries) */

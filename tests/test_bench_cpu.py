@@ -2,6 +2,7 @@
 hierarchical balanced k-means, the kernel-source digest's insensitivity to
 comments and prototypes, and the mode names."""
 import os
+import re
 import shutil
 
 import pytest
@@ -35,7 +36,7 @@ def test_kernel_digest_ignores_comments_and_prototypes(tmp_path, monkeypatch):
     text = hdr.read_text()
     hdr.write_text(text.replace("#endif", "/* a note */\nann_status ann_new_call(ann_index *idx, int32_t x);\n#endif", 1))
     assert bench.kernel_digest() == d0  # a comment and a new prototype
-    hdr.write_text(text.replace("#define ANN_MAX_L 2048", "#define ANN_MAX_L 4096"))
+    hdr.write_text(re.sub(r"#define ANN_MAX_L \d+", "#define ANN_MAX_L 12345", text))
     assert bench.kernel_digest() != d0  # a constant the kernel compiles against
     hdr.write_text(text)
     cu = root / "paper_2506_15986_gb300/csrc/search.cu"

@@ -67,7 +67,7 @@ def test_toy_graphs_exact(golden_dir):
 
 
 @pytest.mark.parametrize("L,W", [(64, 1), (16, 1), (128, 1), (64, 2), (512, 2), (10, 1),
-                                 (64, 3), (128, 4), (512, 4), (1024, 4), (2048, 2)])
+                                 (64, 3), (128, 4), (512, 4), (1024, 4), (2048, 2), (4096, 2)])
 def test_c1_u8_bit_exact(c1, L, W):
     q = c1["queries"]
     k = min(10, L)
