@@ -111,7 +111,7 @@ MEASURED_TRAFFIC = {
     # launch, valid for these kernel sources, entry mode, L, batch and tuned
     # sizes (spill_bits 0: the default for L)
     "shift": [
-        dict(digest="b4972b355968c600", entry="exhaustive", L=93, nq=10_000, hash_bits=-1, stage_rows=8,
+        dict(digest="d2ea997b04bffc6c", entry="exhaustive", L=93, nq=10_000, hash_bits=-1, stage_rows=8,
              team=4, spill_bits=0, bytes=3.576e9 + 0.730e9),
     ],
 }
