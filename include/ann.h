@@ -525,8 +525,8 @@ ann_status ann_topo_tokens(ann_index *idx, const int32_t *d_hubs, int32_t H, int
 
 /*
  * Hierarchical balanced k-means, HBKM (Sec. 4.1, Def. 2 and Algorithm 2), with
- * the hub of every final cluster (Def. 3).  `levels` rounds each split every
- * cluster of the round before (round 0: all n rows) into k children, so
+ * the hub of every final cluster (Def. 3).  `levels` levels each split every
+ * cluster of the level above (level 0: all n rows) into k children, so
  * k^levels clusters come out; child j of cluster c is cluster c*k + j.  A
  * split runs T iterations; each empties the children, visits the cluster's
  * members in increasing row id and puts row x into

@@ -771,8 +771,8 @@ int or_num_threads(void)
 /* Hierarchical balanced k-means, HBKM (Sec. 4.1, Def. 2 and Algorithm 2),   */
 /* and the hub of every final cluster (Def. 3).                              */
 /*                                                                           */
-/* Each of `levels` rounds splits every cluster C of the previous round      */
-/* (round 0: the whole data set) into k children, so k^levels clusters come  */
+/* Each of `levels` levels splits every cluster C of the level above        */
+/* (level 0: the whole data set) into k children, so k^levels clusters come */
 /* out.  A split runs T iterations; each iteration empties the children,     */
 /* then visits C's members in increasing id and puts member x into           */
 /*   j = argmin_j ||x - mu_j||^2 + lam * (2 (c_j - m) + 1)                   */
@@ -784,7 +784,7 @@ int or_num_threads(void)
 /* visit every non-empty child's centroid becomes the mean of its members    */
 /* (an empty child keeps its centroid).  The children start at the members  */
 /* with the min(k, |C|) smallest (key, id), in that order; children past |C| */
-/* stay empty.  Child j of cluster c is cluster c * k + j of the next round. */
+/* stay empty.  Child j of cluster c is cluster c * k + j of the next level. */
 /*                                                                           */
 /* Arithmetic is float32 with every operation rounded on its own (the        */
 /* file's build keeps floating-point contraction off), in these orders:      */
@@ -819,7 +819,7 @@ int or_hbkm(const float *x, int64_t n, int d, int k, int levels, double lambda, 
         if (nc > (int64_t)1 << 30)
             return OR_ERR_ARG;
     }
-    float *cur = (float *)malloc(sizeof(float) * (size_t)d);  /* round-0 centroid */
+    float *cur = (float *)malloc(sizeof(float) * (size_t)d);  /* level-0 centroid */
     float *pc = NULL;                                        /* parents' centroids */
     float *cc = NULL;                                        /* children's centroids */
     int32_t *own = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
@@ -833,7 +833,7 @@ int or_hbkm(const float *x, int64_t n, int d, int k, int levels, double lambda, 
         free(cur); free(own); free(nown); free(mem); free(chl); free(cnt); free(ini); free(sum);
         return OR_ERR_NOMEM;
     }
-    /* round 0: one cluster, the data set, with its mean */
+    /* level 0: one cluster, the data set, with its mean */
     for (int t = 0; t < d; ++t) {
         float s = 0.0f;
         for (int64_t i = 0; i < n; ++i)

@@ -1,8 +1,8 @@
 // hbkm.cu -- hierarchical balanced k-means, HBKM (Sec. 4.1, Def. 2 and
 // Algorithm 2), and the hub of every final cluster (Def. 3).
 //
-// Each of `levels` rounds splits every cluster of the previous round (round
-// 0: the whole data set) into k children.  A split runs T iterations; each
+// Each of `levels` levels splits every cluster of the level above (level 0:
+// the whole data set) into k children.  A split runs T iterations; each
 // iteration empties the children, visits the cluster's members in
 // increasing id and puts member x into
 //     j = argmin_j ||x - mu_j||^2 + lam * (2 (c_j - m) + 1)
@@ -25,7 +25,7 @@
 // Layout: perm[] holds the row ids grouped by current cluster, increasing id
 // inside a cluster; seg[] the clusters' first positions; own[] the cluster of
 // each position.  A split's children keep that order (a stable partition), so
-// each round's members are again in increasing id.
+// each level's members are again in increasing id.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -76,7 +76,7 @@ __device__ void hb_partition_one(int64_t c, int k, const int64_t *seg, const int
 __device__ void hb_hub_one(int64_t c, int lane, const float *x, int dim, const int64_t *seg, const int32_t *perm,
                            const float *cent, int32_t *hubs);
 
-// round 0: the mean of all rows, one thread per coordinate, rows in order
+// level 0: the mean of all rows, one thread per coordinate, rows in order
 __global__ void hb_root(const float *x, int64_t n, int dim, float *cent)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -401,7 +401,7 @@ ann_status ann_hbkm(const float *d_x, int64_t n, int32_t dim, int32_t k, int32_t
     HB_CK(cudaFuncSetAttribute(hb_update, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
     Buf perm(s), perm2(s), own(s), own2(s), seg(s), seg2(s), cent(s), cent2(s), dp(s), D(s), lab(s), cnt(s),
         lamv(s), mv(s), kkv(s), init(s);
-    const int64_t cl_max = nc;  // clusters of the last round; earlier rounds have fewer
+    const int64_t cl_max = nc;  // clusters of the last level; earlier levels have fewer
     HB_CK(perm.alloc(n * 4));
     HB_CK(perm2.alloc(n * 4));
     HB_CK(own.alloc(n * 4));

@@ -50,8 +50,8 @@ def test_matches_oracle_bit_for_bit(k, levels, lam, T):
 
 @pytest.mark.parametrize("n", [9000, 600])
 def test_wide_branching(n):
-    # k = 32, two rounds, 1,024 clusters; at 600 rows the first round's
-    # children hold about 19 rows, fewer than k, so second-round children stay
+    # k = 32, two levels, 1,024 clusters; at 600 rows the first level's
+    # children hold about 19 rows, fewer than k, so second-level children stay
     # empty
     w = synth.shift_f32(n=n, nq=1, n_train=0)
     keys = synth.hbkm_keys(n, seed=8)
@@ -80,7 +80,7 @@ def test_invalid_arguments():
 
 
 def test_full_size_invariants():
-    # the bench's hub extraction: 1M x 128 rows, k = 32, two rounds, T = 10
+    # the bench's hub extraction: 1M x 128 rows, k = 32, two levels, T = 10
     w = synth.shift_f32(n=1_000_000, nq=1, n_train=0)
     x = w["base"]
     keys = synth.hbkm_keys(len(x), seed=synth.SEED_BASE + 13)

@@ -63,7 +63,7 @@ def test_dominant_penalty_balances_every_split():
 
 
 def test_no_penalty_single_split_is_lloyd():
-    # lambda = 0 and one level: T rounds of nearest-centroid assignment and
+    # lambda = 0 and one level: T iterations of nearest-centroid assignment and
     # mean update from the same starting rows, as in or_kmeans
     rng = np.random.default_rng(9)
     centres = np.array([[0, 0, 0], [40, 0, 0], [0, 40, 0], [0, 0, 40], [40, 40, 40]], np.float64)
