@@ -147,3 +147,24 @@ def test_fusion_training_lowers_the_loss():
         ann.ann_trainer_free(t)
     assert ls[-4:].mean() < ls[:4].mean()
     assert not np.array_equal(w0, WO)  # the fusion weights were trained
+
+
+def test_tokens_and_fusion_reject_bad_sizes(built):
+    hubs = torch.zeros(4, dtype=torch.int32, device=DEV)
+    tok = torch.empty((4, 10, 8), dtype=torch.float32, device=DEV)
+    for H, hops, max_nodes in ((0, 3, 64), (4, 0, 64), (4, 65, 64), (4, 3, 0), (4, 3, 8193)):
+        with pytest.raises(ann.AnnError) as e:
+            ann.ann_topo_tokens(built["h"], hubs, H, hops, tok, max_nodes=max_nodes)
+        assert e.value.status == ann.ERR_INVALID_ARG
+    W1, b1, W2, b2, E = synth.model_init(128, 8)
+    t = ann.ann_trainer_create(128, W1, b1, W2, b2, E, 64)
+    try:
+        P = torch.zeros((8, 128), device=DEV)
+        U = torch.zeros((8, 4, 8), device=DEV)
+        for T, dU, heads, dk in ((0, 8, 2, 16), (4, 0, 2, 16), (4, 8, 0, 16), (4, 8, 17, 16)):
+            WQ, WK, WV, WO = _fusion_weights(128, max(dU, 1), max(heads, 1), dk)
+            with pytest.raises(ann.AnnError) as e:
+                ann.ann_trainer_set_fusion(t, P, U, T, dU, heads, dk, WQ, WK, WV, WO)
+            assert e.value.status == ann.ERR_INVALID_ARG
+    finally:
+        ann.ann_trainer_free(t)
