@@ -638,6 +638,27 @@ ann_status ann_build_graph(const void *d_base, int64_t n, int32_t dim, int32_t d
                            int32_t R, float alpha, int32_t *d_graph, int32_t *medoid,
                            int64_t *repairs, void *stream);
 
+/*
+ * The same kind of graph without the O(N^2 d) candidate search, for base sets
+ * of many millions of rows: insertion by search.  The first n_seed rows get
+ * the exact graph above; the rest are inserted in id order, batch rows at a
+ * time: each row of a batch is searched on the graph built so far (beam
+ * search as ann_search_batch, from the seed graph's navigating node, pool
+ * max(K, 64), W = 4), its K nearest found become its candidates and are
+ * pruned to R as in step 2; then each node those rows point to takes them
+ * back, appended while its row has room, else its neighbours and the (at
+ * most 32 per batch) newcomers are sorted by (squared L2, id) and pruned to R
+ * again.  Finally the navigating node of all rows and the repair of step 3.
+ * Rows of one batch do not see each other; which newcomers a busy node keeps
+ * can vary from run to run (they arrive through atomics).
+ *   dtype must be ANN_F32 (else ANN_ERR_UNSUPPORTED); R <= 32; K + 1 <=
+ *   n_seed <= n; batch >= 1; other arguments as for ann_build_graph.
+ * Blocking.
+ */
+ann_status ann_build_graph_insert(const void *d_base, int64_t n, int32_t dim, int32_t dtype, int32_t K, int32_t R,
+                                  float alpha, int64_t n_seed, int64_t batch, int32_t *d_graph, int32_t *medoid,
+                                  int64_t *repairs, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -101,6 +101,8 @@ def load_library(path: str | None = None):
         "ann_kmeans": ([_p, i64, i32, i32, _p, i64, i32, _p, i32, _p, _p, _p], i32),
         "ann_assign_hubs": ([_p, i64, i32, i32, _p, i32, _p, _p, _p], i32),
         "ann_hbkm": ([_p, i64, i32, i32, i32, _c.c_double, i32, _p, _p, _p, _p, _p], i32),
+        "ann_build_graph_insert": ([_p, i64, i32, i32, i32, i32, _c.c_float, i64, i64, _p, _c.POINTER(i32),
+                                    _c.POINTER(i64), _p], i32),
         "ann_topo_tokens": ([_p, _p, i32, i32, i32, _p, _p, _p], i32),
         "ann_trainer_set_fusion": ([_p, _p, _p, i32, i32, i32, i32, _p, _p, _p, _p], i32),
         "ann_trainer_get_fusion": ([_p, _p, _p, _p, _p, i32], i32),
@@ -232,6 +234,17 @@ def ann_medoid(base, n, dim, dtype, stream=None) -> int:
     _check(load_library().ann_medoid(_ptr(base), int(n), int(dim), int(dtype), ctypes.byref(m),
                                      _stream(stream)), "ann_medoid")
     return m.value
+
+
+def ann_build_graph_insert(base, n, dim, dtype, K, R, alpha, n_seed, batch, graph, medoid=-1, stream=None):
+    """Build the graph by insertion by search (blocking).  Returns (medoid, repairs)."""
+    m = _c.c_int32(int(medoid))
+    rep = _c.c_int64(0)
+    _check(load_library().ann_build_graph_insert(_ptr(base), int(n), int(dim), int(dtype), int(K), int(R),
+                                                 float(alpha), int(n_seed), int(batch), _ptr(graph),
+                                                 ctypes.byref(m), ctypes.byref(rep), _stream(stream)),
+           "ann_build_graph_insert")
+    return m.value, rep.value
 
 
 def ann_build_graph(base, n, dim, dtype, K, R, alpha, graph, medoid=-1, stream=None):

@@ -563,11 +563,14 @@ ann_status medoid_gpu(const void *d_base, int64_t n, int dim, int dtype, cudaStr
     return ANN_OK;
 }
 
+ann_status prune_rows(const void *d_base, int64_t n, int dim, int dtype, int K, int R, float alpha,
+                      const int32_t *cand, const void *cand_d, int32_t *d_graph, cudaStream_t s);
+ann_status repair_reachability(const void *d_base, int64_t n, int dim, int dtype, int R, int32_t *d_graph,
+                               int32_t medoid_id, int64_t *repairs, cudaStream_t s);
+
 ann_status build_graph_gpu(const void *d_base, int64_t n, int dim, int dtype, int K, int R, float alpha,
                            int32_t *d_graph, int32_t *medoid, int64_t *repairs, cudaStream_t s)
 {
-    const int es = elem_size(dtype);
-    const int rowbytes = dim * es;
     // 1. exact K-NN candidates of every node (itself excluded)
     DevBuf<int32_t> cids;
     DevBuf<float> cd;
@@ -577,6 +580,22 @@ ann_status build_graph_gpu(const void *d_base, int64_t n, int dim, int dtype, in
     if (st != ANN_OK)
         return st;
     // 2. relative-neighbourhood pruning
+    if ((st = prune_rows(d_base, n, dim, dtype, K, R, alpha, cids.p, cd.p, d_graph, s)) != ANN_OK)
+        return st;
+    // 3. navigating node
+    if (*medoid < 0 && (st = medoid_gpu(d_base, n, dim, dtype, s, medoid)) != ANN_OK)
+        return st;
+    // 4. reachability repair
+    return repair_reachability(d_base, n, dim, dtype, R, d_graph, *medoid, repairs, s);
+}
+
+// Relative-neighbourhood pruning of n candidate rows (K per row, ascending
+// (distance, id), -1 pads at the end) into the n adjacency rows at d_graph.
+ann_status prune_rows(const void *d_base, int64_t n, int dim, int dtype, int K, int R, float alpha,
+                      const int32_t *cand, const void *cand_d, int32_t *d_graph, cudaStream_t s)
+{
+    const int es = elem_size(dtype);
+    const int rowbytes = dim * es;
     int s16 = rowbytes / 16;
     if ((s16 & 1) == 0)
         s16 += 1;
@@ -589,7 +608,7 @@ ann_status build_graph_gpu(const void *d_base, int64_t n, int dim, int dtype, in
     do {                                                                                                       \
         CK(cudaFuncSetAttribute(rng_prune<DT, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,               \
                                 static_cast<int>(smem)));                                                      \
-        rng_prune<DT, ST><<<grid, 32, smem, s>>>(bb, rowbytes, dim, n, cids.p, cd.p, K, R, alpha, stride,      \
+        rng_prune<DT, ST><<<grid, 32, smem, s>>>(bb, rowbytes, dim, n, cand, cand_d, K, R, alpha, stride,      \
                                                  d_graph);                                                     \
     } while (0)
     if (dtype == ANN_U8 && staged)
@@ -601,16 +620,17 @@ ann_status build_graph_gpu(const void *d_base, int64_t n, int dim, int dtype, in
     else
         PRUNE(ANN_F32, false);
 #undef PRUNE
-    CK(cudaGetLastError());
-    // 3. navigating node
-    if (*medoid < 0) {
-        st = medoid_gpu(d_base, n, dim, dtype, s, medoid);
-        if (st != ANN_OK)
-            return st;
-    }
-    // 4. reachability repair: nodes in id order; an unreachable node u gets the
-    // edge w -> u from the nearest reachable node w with a free slot; all that
-    // u reaches becomes reachable before the next node is taken
+    return cuda_status(cudaGetLastError());
+}
+
+// Reachability repair: nodes in id order; an unreachable node u gets the edge
+// w -> u from the nearest reachable node w with a free slot; all that u
+// reaches becomes reachable before the next node is taken.
+ann_status repair_reachability(const void *d_base, int64_t n, int dim, int dtype, int R, int32_t *d_graph,
+                               int32_t medoid_id, int64_t *repairs, cudaStream_t s)
+{
+    const int rowbytes = dim * elem_size(dtype);
+    const int32_t *medoid = &medoid_id;
     std::vector<int32_t> g(static_cast<size_t>(n) * R);
     CK(cudaMemcpyAsync(g.data(), d_graph, g.size() * 4, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -699,6 +719,153 @@ ann_status build_graph_gpu(const void *d_base, int64_t n, int dim, int dtype, in
     return ANN_OK;
 }
 
+namespace {
+
+constexpr int kInbox = 32;  // reverse-edge requests kept per node and batch
+
+// every new node's out-edges become requests in their targets' inboxes
+__global__ void reverse_collect(const int32_t *rows, int64_t b0, int64_t nb, int R, int32_t *inbox, int32_t *cnt,
+                                int32_t *touched, int32_t *ntouched)
+{
+    const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (t >= nb * R)
+        return;
+    const int32_t q = rows[t];
+    if (q < 0)
+        return;
+    const int slot = atomicAdd(&cnt[q], 1);
+    if (slot == 0)
+        touched[atomicAdd(ntouched, 1)] = q;
+    if (slot < kInbox)
+        inbox[static_cast<int64_t>(q) * kInbox + slot] = static_cast<int32_t>(b0 + t / R);
+}
+
+// A touched node's row: its neighbours plus its inbox; appended while they
+// fit, else all of them sorted by (squared L2, id) and pruned to R as
+// rng_prune does.  One warp per node (R <= 32: lane j holds slot j of the
+// row and inbox entry j).
+__global__ void reverse_prune(const float *x, int dim, const int32_t *touched, const int32_t *ntouched,
+                              const int32_t *inbox, int32_t *cnt, int R, float alpha, int32_t *graph)
+{
+    __shared__ uint64_t keys[64];
+    __shared__ int32_t kept[32];
+    const int lane = threadIdx.x;
+    const int nt = *ntouched;
+    const uint8_t *xb = reinterpret_cast<const uint8_t *>(x);
+    const int rowbytes = dim * 4;
+    for (int w = blockIdx.x; w < nt; w += gridDim.x) {
+        const int32_t q = touched[w];
+        const int nin = min(cnt[q], kInbox);
+        const int32_t c0 = lane < R ? graph[static_cast<int64_t>(q) * R + lane] : -1;
+        const int32_t c1 = lane < nin ? inbox[static_cast<int64_t>(q) * kInbox + lane] : -1;
+        const int deg = __popc(__ballot_sync(kFull, c0 >= 0));
+        if (deg + nin <= R) {
+            if (lane < nin)
+                graph[static_cast<int64_t>(q) * R + deg + lane] = c1;
+        } else {
+            const uint8_t *xq = xb + static_cast<int64_t>(q) * rowbytes;
+            uint64_t k0 = c0 >= 0 ? make_key(exact_dist_bits<ANN_F32, ANN_L2>(xb + static_cast<int64_t>(c0) * rowbytes,
+                                                                               xq, dim), c0)
+                                  : kKeyMax;
+            uint64_t k1 = c1 >= 0 ? make_key(exact_dist_bits<ANN_F32, ANN_L2>(xb + static_cast<int64_t>(c1) * rowbytes,
+                                                                               xq, dim), c1)
+                                  : kKeyMax;
+            warp_sort64(k0, k1, lane);
+            keys[lane] = k0;
+            keys[lane + 32] = k1;
+            __syncwarp();
+            int nk = 0;
+            for (int c = 0; c < 64 && nk < R; ++c) {
+                const uint64_t kc = keys[c];
+                if (kc == kKeyMax)
+                    break;
+                const int32_t id = key_id(kc);
+                const float dqc = ord_to_f32(static_cast<uint32_t>(kc >> 32));
+                bool pruned = false;
+                for (int j = lane; j < nk; j += 32)
+                    pruned |= alpha * ord_to_f32(exact_dist_bits<ANN_F32, ANN_L2>(
+                                          xb + static_cast<int64_t>(kept[j]) * rowbytes,
+                                          xb + static_cast<int64_t>(id) * rowbytes, dim)) <= dqc;
+                if (!__any_sync(kFull, pruned)) {
+                    if (lane == 0)
+                        kept[nk] = id;
+                    ++nk;
+                }
+                __syncwarp();
+            }
+            if (lane < R)
+                graph[static_cast<int64_t>(q) * R + lane] = lane < nk ? kept[lane] : -1;
+        }
+        __syncwarp();
+        if (lane == 0)
+            cnt[q] = 0;
+    }
+}
+
+}  // namespace
+
+// Insertion by search: the exact graph of the first n0 rows, then batches of
+// rows each searched on the graph built so far (their k nearest found become
+// their candidates, pruned to R), with the reverse edges added or re-pruned;
+// then the navigating node of all rows and the reachability repair.
+ann_status build_graph_insert(const float *x, int64_t n, int dim, int K, int R, float alpha, int64_t n0,
+                              int64_t batch, int32_t *d_graph, int32_t *medoid, int64_t *repairs, cudaStream_t s)
+{
+    int device = 0;
+    CK(cudaGetDevice(&device));
+    int32_t m0 = -1;
+    ann_status st = build_graph_gpu(x, n0, dim, ANN_F32, K, R, alpha, d_graph, &m0, nullptr, s);
+    if (st != ANN_OK)
+        return st;
+    CK(cudaMemsetAsync(d_graph + n0 * R, 0xff, static_cast<size_t>(n - n0) * R * 4, s));
+    DevBuf<int32_t> inbox, cnt, touched, ntouched, ids;
+    DevBuf<float> dd;
+    CK(inbox.alloc(static_cast<size_t>(n) * kInbox, s));
+    CK(cnt.alloc(n, s));
+    CK(touched.alloc(n, s));
+    CK(ntouched.alloc(1, s));
+    CK(ids.alloc(static_cast<size_t>(batch) * K, s));
+    CK(dd.alloc(static_cast<size_t>(batch) * K, s));
+    CK(cudaMemsetAsync(cnt.p, 0, n * 4, s));
+    ann_search_params p{};
+    p.k = K;
+    p.L = std::max(K, 64);
+    p.W = R <= 32 ? 4 : 2;
+    for (int64_t b0 = n0; b0 < n; b0 += batch) {
+        const int64_t nb = std::min(batch, n - b0);
+        // the graph so far (rows past b0 are empty, so unreachable)
+        ann_index_desc desc{};
+        desc.n = n;
+        desc.dim = dim;
+        desc.degree = R;
+        desc.dtype = ANN_F32;
+        desc.metric = ANN_L2;
+        desc.base = x;
+        desc.graph = d_graph;
+        desc.medoid = m0;
+        CK(cudaStreamSynchronize(s));
+        ann_index *idx = nullptr;
+        if ((st = ann_index_create(&desc, device, &idx)) != ANN_OK)
+            return st;
+        st = ann_search_batch(idx, x + b0 * dim, nb, nullptr, &p, ids.p, dd.p, nullptr, s);
+        if (st == ANN_OK)
+            st = ann_sync_status(idx, s);
+        ann_free_index(idx);
+        if (st != ANN_OK)
+            return st;
+        if ((st = prune_rows(x, nb, dim, ANN_F32, K, R, alpha, ids.p, dd.p, d_graph + b0 * R, s)) != ANN_OK)
+            return st;
+        CK(cudaMemsetAsync(ntouched.p, 0, 4, s));
+        reverse_collect<<<static_cast<unsigned>((nb * R + 255) / 256), 256, 0, s>>>(
+            d_graph + b0 * R, b0, nb, R, inbox.p, cnt.p, touched.p, ntouched.p);
+        reverse_prune<<<152 * 8, 32, 0, s>>>(x, dim, touched.p, ntouched.p, inbox.p, cnt.p, R, alpha, d_graph);
+        CK(cudaGetLastError());
+    }
+    if (*medoid < 0 && (st = medoid_gpu(x, n, dim, ANN_F32, s, medoid)) != ANN_OK)
+        return st;
+    return repair_reachability(x, n, dim, ANN_F32, R, d_graph, *medoid, repairs, s);
+}
+
 }  // namespace ann
 
 using namespace ann;
@@ -732,6 +899,22 @@ ann_status ann_medoid(const void *d_base, int64_t n, int32_t dim, int32_t dtype,
     if (!d_base || !medoid || n < 1 || n > INT32_MAX || dim < 1)
         return ANN_ERR_INVALID_ARG;
     return medoid_gpu(d_base, n, dim, dtype, static_cast<cudaStream_t>(stream), medoid);
+}
+
+ann_status ann_build_graph_insert(const void *d_base, int64_t n, int32_t dim, int32_t dtype, int32_t K, int32_t R,
+                                  float alpha, int64_t n_seed, int64_t batch, int32_t *d_graph, int32_t *medoid,
+                                  int64_t *repairs, void *stream)
+{
+    if (!d_base || !d_graph || !medoid || n < 2 || n > INT32_MAX || dim < 4 || K < 1 || K > 128 || R < 1 ||
+        R > K || R > 32 || !(alpha > 0.f) || n_seed < K + 1 || n_seed > n || batch < 1 || *medoid >= n)
+        return ANN_ERR_INVALID_ARG;
+    if (dtype != ANN_F32)
+        return ANN_ERR_UNSUPPORTED;
+    if ((static_cast<int64_t>(dim) * 4) % 16 != 0 || (reinterpret_cast<uintptr_t>(d_base) & 15))
+        return ANN_ERR_INVALID_ARG;
+    return build_graph_insert(static_cast<const float *>(d_base), n, dim, K, R, alpha, n_seed,
+                              std::min<int64_t>(batch, n), d_graph, medoid, repairs,
+                              static_cast<cudaStream_t>(stream));
 }
 
 ann_status ann_build_graph(const void *d_base, int64_t n, int32_t dim, int32_t dtype, int32_t K, int32_t R,

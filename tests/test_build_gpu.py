@@ -102,3 +102,44 @@ def test_graph_f32_agreement():
                 seen[u] = True
                 st.append(u)
     assert seen.all()
+
+
+def test_insertion_graph_builder():
+    # insertion by search: a seed of 15,000 rows built exactly, 45,000 more
+    # inserted in batches of 15,000; the graph is valid and reachable, and a
+    # search on it reaches the exact graph's recall
+    from gpu_util import search
+    w = synth.shift_f32(n=60000, nq=500, n_train=0)
+    x = torch.from_numpy(w["base"]).to(DEV)
+    n, d = w["base"].shape
+    g_in = torch.empty((n, 32), dtype=torch.int32, device=DEV)
+    g_ex = torch.empty((n, 32), dtype=torch.int32, device=DEV)
+    med_i, _ = ann.ann_build_graph_insert(x, n, d, ann.F32, 64, 32, 1.0, 15000, 15000, g_in)
+    med_e, _ = ann.ann_build_graph(x, n, d, ann.F32, 64, 32, 1.0, g_ex)
+    assert med_i == med_e  # the navigating node does not depend on the edges
+    gi = g_in.cpu().numpy()
+    assert ((gi >= -1) & (gi < n)).all() and (gi != np.arange(n)[:, None]).all()
+    assert all(len(set(r[r >= 0])) == (r >= 0).sum() for r in gi[::97])  # no repeated edge
+    seen = np.zeros(n, bool)
+    seen[med_i] = True
+    front = np.array([med_i])
+    while len(front):
+        nxt = gi[front].ravel()
+        nxt = np.unique(nxt[nxt >= 0])
+        nxt = nxt[~seen[nxt]]
+        seen[nxt] = True
+        front = nxt
+    assert seen.all()
+    q = w["queries"]
+    truth, _ = oracle.knn(w["base"], q.astype(np.float64), 10)
+    rec = []
+    for g, med in ((g_in, med_i), (g_ex, med_e)):
+        h = ann.ann_index_create(x, g, med, ann.F32, ann.L2)
+        try:
+            ids, *_ = search(h, q, 10, 64, W=2)
+        finally:
+            ann.ann_free_index(h)
+        rec.append(np.mean([len(np.intersect1d(a, b)) / 10 for a, b in zip(ids, truth)]))
+    assert rec[0] >= rec[1] - 0.02, rec
+    with pytest.raises(ann.AnnError):
+        ann.ann_build_graph_insert(x, n, d, ann.F32, 64, 48, 1.0, 15000, 15000, g_in)  # R > 32
