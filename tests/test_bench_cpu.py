@@ -50,3 +50,12 @@ def test_mode_names():
     assert bench.mode_info(A, "medoid") == (0, 1)
     assert bench.mode_info(A, "learned") == (1, 1)
     assert bench.mode_info(A, "exhaustive_s8") == (2, 8)
+
+
+def test_batch10m_spec(monkeypatch):
+    monkeypatch.setattr("sys.argv", ["bench.py", "--workload", "batch10m"])
+    args = bench.parse()
+    spec = args.spec
+    assert spec["n"] == 10_000_000 and spec["dim"] == 96 and spec["nq"] == 100_000
+    assert spec["insert"] == (1_000_000, 1_000_000) and spec["gt_rows"] == 5_000
+    assert spec["batching"] and spec["hubs"] == 16384
