@@ -641,10 +641,11 @@ ann_status ann_build_graph(const void *d_base, int64_t n, int32_t dim, int32_t d
 /*
  * The same kind of graph without the O(N^2 d) candidate search, for base sets
  * of many millions of rows: insertion by search.  The first n_seed rows get
- * the exact graph above; the rest are inserted in id order, batch rows at a
- * time: each row of a batch is searched on the graph built so far (beam
+ * the exact graph above; the rest are inserted in id order, in batches of at
+ * most `batch` rows and at most a quarter of the rows inserted before them:
+ * each row of a batch is searched on the graph built so far (beam
  * search as ann_search_batch, from the seed graph's navigating node, pool
- * max(K, 64), W = 4), its K nearest found become its candidates and are
+ * max(K, 128), W = 4), its K nearest found become its candidates and are
  * pruned to R as in step 2; then each node those rows point to takes them
  * back, appended while its row has room, else its neighbours and the (at
  * most 32 per batch) newcomers are sorted by (squared L2, id) and pruned to R

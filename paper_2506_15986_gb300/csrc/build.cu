@@ -829,10 +829,12 @@ ann_status build_graph_insert(const float *x, int64_t n, int dim, int K, int R, 
     CK(cudaMemsetAsync(cnt.p, 0, n * 4, s));
     ann_search_params p{};
     p.k = K;
-    p.L = std::max(K, 64);
+    p.L = std::max(K, 128);
     p.W = R <= 32 ? 4 : 2;
-    for (int64_t b0 = n0; b0 < n; b0 += batch) {
-        const int64_t nb = std::min(batch, n - b0);
+    for (int64_t b0 = n0, nb = 0; b0 < n; b0 += nb) {
+        // a batch holds at most a quarter of the rows inserted so far: rows of
+        // one batch do not see each other
+        nb = std::min({batch, n - b0, std::max<int64_t>(1, b0 / 4)});
         // the graph so far (rows past b0 are empty, so unreachable)
         ann_index_desc desc{};
         desc.n = n;
