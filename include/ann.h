@@ -167,10 +167,16 @@ const char *ann_status_string(ann_status s);
  * [-1, n) and the medoid in [0, n).  Returns ANN_ERR_INVALID_ARG on bad
  * arguments, ANN_ERR_OOM / ANN_ERR_CUDA on device failures; *out is set only
  * on success.
+ * The index holds the base set D and its proximity graph G of Sec. 2.1
+ * (Def. 1).
  */
 ann_status ann_index_create(const ann_index_desc *desc, int device, ann_index **out);
 
-/* Bytes of one packed ANN_I8S row of dim codes: 16 + dim rounded up to 16. */
+/*
+ * Bytes of one packed ANN_I8S row of dim codes: 16 + dim rounded up to 16.
+ * Layout of the int8 storage of the precision line; pure arithmetic, no
+ * error (0 for dim < 1).
+ */
 int32_t ann_i8s_row_bytes(int32_t dim);
 
 /*
@@ -180,15 +186,22 @@ int32_t ann_i8s_row_bytes(int32_t dim);
  * 127; code_j = x_j / scale rounded half to even and clipped to [-127, 127];
  * an all-zero row gets scale 0 and zero codes.  dim must be a multiple of 4.
  * Asynchronous on stream.
+ * The int8-with-scale storage of the precision line (a spec choice;
+ * the paper fixes no precision).
  */
 ann_status ann_quantize_i8s(const float *d_x, int64_t n, int32_t dim, void *d_rows, void *stream);
 
-/* Free an index and its device memory (NULL is accepted).  Synchronises the device. */
+/*
+ * Free an index and its device memory (NULL is accepted).  Synchronises the device.
+ * Lifetime only (no paper passage); always ANN_OK.
+ */
 ann_status ann_free_index(ann_index *idx);
 
 /*
  * Read index metadata; any output pointer may be NULL.  has_model reports
  * whether a learned entry model is attached.
+ * Metadata of the Sec. 2.1 index; ANN_ERR_INVALID_ARG for a NULL index,
+ * else ANN_OK.
  */
 ann_status ann_index_info(const ann_index *idx, int64_t *n, int32_t *dim, int32_t *degree,
                           int32_t *dtype, int32_t *metric, int32_t *medoid,
@@ -197,6 +210,8 @@ ann_status ann_index_info(const ann_index *idx, int64_t *n, int32_t *dim, int32_
 /*
  * Write the index (header, base, graph, optional fp32 copy, entry model) to
  * `path` with a 64-bit FNV-1a checksum.  ANN_ERR_IO on a write failure.
+ * Persistence of the Sec. 2.1 index and the Sec. 4.3 model (no paper
+ * passage).
  */
 ann_status ann_save_index(const ann_index *idx, const char *path);
 
@@ -204,6 +219,8 @@ ann_status ann_save_index(const ann_index *idx, const char *path);
  * Load an index written by ann_save_index onto `device`.  ANN_ERR_IO if the
  * file cannot be read, ANN_ERR_FORMAT if its magic, version, sizes or checksum
  * do not match (a truncated or corrupted file).
+ * Persistence of the Sec. 2.1 index and the Sec. 4.3 model (no paper
+ * passage).
  */
 ann_status ann_load_index(const char *path, int device, ann_index **out);
 
@@ -226,6 +243,10 @@ ann_status ann_load_index(const char *path, int device, ann_index **out);
  * streams may run concurrently on one index (their outputs must not alias),
  * which lets the next batch's grid fill the SMs that one batch's last
  * queries leave idle.
+ * Asynchronous on `stream`. Errors: ANN_ERR_INVALID_ARG for a NULL or
+ * misaligned pointer or parameters out of range (returned before any
+ * launch); device-side capacity, timeout and bad-input conditions go to the
+ * status word (ann_sync_status) and their queries return ids -1.
  */
 ann_status ann_search_batch(ann_index *idx, const void *d_queries, int64_t nq,
                             const int32_t *d_entry, const ann_search_params *p,
@@ -235,6 +256,7 @@ ann_status ann_search_batch(ann_index *idx, const void *d_queries, int64_t nq,
  * Synchronise `stream`, then return and clear the index's device status
  * word: ANN_OK, or the first of ANN_ERR_CAPACITY / ANN_ERR_TIMEOUT raised by
  * kernels since the last call; ANN_ERR_CUDA if a CUDA call failed.
+ * The device status word of the Sec. 2.1 search (no paper passage).
  */
 ann_status ann_sync_status(ann_index *idx, void *stream);
 
@@ -257,10 +279,17 @@ ann_status ann_plan_create(ann_index *idx, const void *d_queries, int64_t nq, in
                            int32_t L_hub, const ann_search_params *p, int32_t *d_entry_buf,
                            int32_t *d_ids, void *d_dists, int32_t *d_stats, ann_plan **out);
 
-/* Launch a captured batch on `stream` (asynchronous). */
+/*
+ * Launch a captured batch on `stream` (asynchronous).
+ * The batching line (the benchmark spec): one captured batch of Sec. 4.3 entry
+ * selection and Sec. 2.1 search. ANN_ERR_INVALID_ARG for a NULL plan.
+ */
 ann_status ann_plan_launch(ann_plan *plan, void *stream);
 
-/* Free a plan (NULL is accepted).  Synchronises the device. */
+/*
+ * Free a plan (NULL is accepted).  Synchronises the device.
+ * Lifetime only (no paper passage); always ANN_OK.
+ */
 ann_status ann_plan_free(ann_plan *plan);
 
 /*
@@ -283,6 +312,8 @@ ann_status ann_plan_free(ann_plan *plan);
  * by FP32 rounding.  Blocking.  Errors: ANN_ERR_INVALID_ARG for a NULL index,
  * params or best, nq < 1, reps < 1 or lanes outside 1..8; a search error
  * stops the tuning and is returned.
+ * The batching line's autotuner (the benchmark spec); speed knobs of the Sec. 2.1
+ * search only.
  */
 ann_status ann_autotune(ann_index *idx, const void *d_queries, int64_t nq, const int32_t *d_entry,
                         const ann_search_params *p, int32_t *d_ids, void *d_dists, int32_t reps,
@@ -339,6 +370,7 @@ ann_status ann_set_entry_model(ann_index *idx, const ann_entry_model_desc *model
 /*
  * Copy the attached model out (host or device destinations; NULL skips an
  * array).  Sizes as in ann_entry_model_desc.  ANN_ERR_INVALID_ARG without a model.
+ * The Sec. 4.3 two-tower model and its hub graph.
  */
 ann_status ann_get_entry_model(const ann_index *idx, float *W1, float *b1, float *W2, float *b2,
                                float *hub_emb, int32_t *hub_nodes, int32_t *hub_graph,
@@ -399,7 +431,10 @@ ann_status ann_select_entries(ann_index *idx, const void *d_queries, int64_t nq,
 ann_status ann_select_entry_noalloc(ann_index *idx, const void *d_queries, int64_t nq,
                                     int32_t *d_entry, float *d_qhat, void *stream);
 
-/* Largest nq ann_select_entry_noalloc accepts. */
+/*
+ * Largest nq ann_select_entry_noalloc accepts.
+ * A constant of this implementation (no paper passage); no error.
+ */
 int64_t ann_select_entry_noalloc_max_queries(void);
 
 /* ---- entry-model training (Sec. 4.2 labels, Sec. 4.3 loss, Sec. 5.1 Adam) -- */
@@ -414,6 +449,8 @@ typedef struct ann_trainer ann_trainer;
  *   tau        InfoNCE temperature; lr, beta1, beta2, eps: Adam
  * Every GEMM of a step runs on the tensor cores (BF16 operands, FP32
  * accumulators); parameters, gradients and Adam state are fp32.
+ * Blocking; ANN_ERR_INVALID_ARG for NULL weights or sizes out of range,
+ * ANN_ERR_CUDA for a bad device, ANN_ERR_OOM.
  */
 ann_status ann_trainer_create(int device, int32_t in_dim, int32_t n_hubs, const float *W1, const float *b1,
                               const float *W2, const float *b2, const float *hub_emb, int64_t max_batch,
@@ -427,6 +464,9 @@ ann_status ann_trainer_free(ann_trainer *t);
  * query row (+1 positive, -1 negative, 0 unused).  Computes the loss and the
  * gradients of every parameter; applies the Adam update when apply_update is
  * non-zero.  loss_out (host, optional) receives the batch loss (blocking).
+ * Sec. 4.3 Eq. loss and its gradient, Sec. 5.1 Adam. Blocking when loss_out
+ * is given, else asynchronous; ANN_ERR_INVALID_ARG for a NULL or misaligned
+ * input or nb out of range.
  */
 ann_status ann_trainer_step(ann_trainer *t, const float *d_queries, const int32_t *d_rows, int64_t nb,
                             const int8_t *d_mask, int32_t apply_update, float *loss_out, void *stream);
@@ -436,6 +476,7 @@ ann_status ann_trainer_step(ann_trainer *t, const float *d_queries, const int32_
  * d_order[e*nt .. e*nt+nt) (device, NULL = 0..nt-1) in batches of max_batch.
  * d_losses (device, optional) receives epochs * ceil(nt / max_batch) batch
  * losses.  Blocking.
+ * Sec. 4.3 training with Sec. 5.1 Adam.
  */
 ann_status ann_trainer_fit(ann_trainer *t, const float *d_queries, int64_t nt, const int8_t *d_mask,
                            const int32_t *d_order, int32_t epochs, float *d_losses, void *stream);
@@ -444,6 +485,8 @@ ann_status ann_trainer_fit(ann_trainer *t, const float *d_queries, int64_t nt, c
  * Copy the current parameters (gradients != 0: the last step's gradients).
  * With a fusion tower, hub_emb receives the rows the model scores, E + F,
  * and its gradient is that of E + F (the same as E's).
+ * Sec. 4.3 model parameters. Blocking; ANN_ERR_TIMEOUT if a tensor-core
+ * wait of an earlier step gave up, ANN_ERR_INVALID_ARG for a NULL trainer.
  */
 ann_status ann_trainer_get(const ann_trainer *t, float *W1, float *b1, float *W2, float *b2, float *hub_emb,
                            int32_t gradients);
@@ -466,10 +509,18 @@ ann_status ann_trainer_set_fusion(ann_trainer *t, const float *d_hub_vecs, const
                                   int32_t token_dim, int32_t heads, int32_t head_dim, const float *WQ, const float *WK,
                                   const float *WV, const float *WO);
 
-/* The fusion weights (gradients != 0: the last step's gradients), as laid out for ann_trainer_set_fusion. */
+/*
+ * The fusion weights (gradients != 0: the last step's gradients), as laid out for ann_trainer_set_fusion.
+ * Sec. 4.3 Eq. fusion weights. Blocking; ANN_ERR_INVALID_ARG without a
+ * fusion tower.
+ */
 ann_status ann_trainer_get_fusion(const ann_trainer *t, float *WQ, float *WK, float *WV, float *WO, int32_t gradients);
 
-/* Attach the trained model to an index (see ann_set_entry_model). */
+/*
+ * Attach the trained model to an index (see ann_set_entry_model).
+ * The Sec. 4.3 model and its hub graph (cosine, s neighbours). Blocking;
+ * errors as ann_set_entry_model.
+ */
 ann_status ann_trainer_attach(const ann_trainer *t, ann_index *idx, const int32_t *hub_nodes,
                               int32_t hub_degree, void *stream);
 
@@ -477,6 +528,7 @@ ann_status ann_trainer_attach(const ann_trainer *t, ann_index *idx, const int32_
  * One Adam update with bias correction at step `step` (>= 1) over n fp32
  * parameters: m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
  * p -= lr (m / (1-b1^step)) / (sqrt(v / (1-b2^step)) + eps).  Asynchronous.
+ * Sec. 5.1 names Adam (Kingma and Ba's update).
  */
 ann_status ann_adam_update(float *d_params, const float *d_grads, float *d_m, float *d_v, int64_t n, int64_t step,
                            float lr, float beta1, float beta2, float eps, void *stream);
@@ -583,6 +635,7 @@ ann_status ann_hub_costs(ann_index *idx, const void *d_queries, int64_t nq, cons
  * hops <= m + t_pos, -1 if hops >= m + t_neg or never reached, 0 otherwise;
  * hubs not searched are -1; a query with no reached hub gets an all -1 row.
  *   d_mask out: nq*n_hubs int8; d_best out (optional): nq int32.  Asynchronous.
+ * Sec. 4.2, Def. 4 and the labelling rule after it (t_pos, t_neg).
  */
 ann_status ann_hub_labels(const int32_t *d_evals, const int32_t *d_hops, const int32_t *d_cand, int64_t nq,
                           int32_t M, int32_t n_hubs, int32_t t_pos, int32_t t_neg, int8_t *d_mask,
@@ -655,6 +708,8 @@ ann_status ann_build_graph(const void *d_base, int64_t n, int32_t dim, int32_t d
  *   dtype must be ANN_F32 (else ANN_ERR_UNSUPPORTED); R <= 32; K + 1 <=
  *   n_seed <= n; batch >= 1; other arguments as for ann_build_graph.
  * Blocking.
+ * Sec. 2.1, Def. 1 (the proximity graph); the insertion order is this
+ * implementation's.
  */
 ann_status ann_build_graph_insert(const void *d_base, int64_t n, int32_t dim, int32_t dtype, int32_t K, int32_t R,
                                   float alpha, int64_t n_seed, int64_t batch, int32_t *d_graph, int32_t *medoid,
