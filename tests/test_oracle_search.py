@@ -199,3 +199,21 @@ def test_seed_sets():
     ids, d, _, _ = oracle.search(base, g, q, np.array([[med, 3, 77]] * 12, np.int32), 400, 5)
     tid, td = oracle.knn(base, q, 5)
     assert np.array_equal(ids, tid)
+
+
+def test_ip_search_with_full_pool_is_exact_mips():
+    # maximum inner product: with L >= N on a connected graph every node is
+    # evaluated, so the result is the exact top-k by inner product (largest
+    # first), which oracle.knn gives and a float64 matmul pins
+    rng = np.random.default_rng(21)
+    x = rng.standard_normal((300, 16))
+    x /= np.linalg.norm(x, axis=1, keepdims=True)
+    x = x.astype(np.float32)
+    g, _ = oracle.build_graph(x, K=24, R=12)
+    q = rng.standard_normal((20, 16))
+    ids, d, ev, hp = oracle.search(x, g, q, 0, 300, 10, metric=oracle.IP)
+    S = q @ x.astype(np.float64).T
+    ref = np.argsort(-S, axis=1, kind="stable")[:, :10]
+    assert np.array_equal(ids, ref)
+    assert (ev == 300).all()
+    np.testing.assert_allclose(-d, np.take_along_axis(S, ref, 1), rtol=1e-12, atol=1e-12)

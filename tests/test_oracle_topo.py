@@ -146,3 +146,14 @@ def test_fusion_single_token_closed_form():
     np.testing.assert_allclose(F, (U[:, 0] @ WV) @ WO, rtol=1e-12, atol=1e-12)
     dWQ, dWK, dWV, dWO = ot.fusion_backward(np.ones_like(F), cache, WO)
     assert np.abs(dWQ).max() < 1e-12 and np.abs(dWK).max() < 1e-12
+
+
+def test_size_cap_on_the_hand_walk():
+    # the same walk stopped at 3 nodes: hub 0, then 1 and 3 at hop 1; node 2
+    # (hop 2) never joins, so the hop-2 token holds only its positional entries
+    tok, nodes = oracle.topo_tokens(X7, G7, [0], 2, max_nodes=3)
+    assert nodes.tolist() == [3]
+    f = np.float32
+    np.testing.assert_array_equal(tok[0, 0, :2], [f(1) / f(3), 1])
+    np.testing.assert_array_equal(tok[0, 1, :2], [f(2) / f(3), f(4) / f(8)])
+    np.testing.assert_array_equal(tok[0, 2], np.array([0, 0, 0, 0, 0, 0, 1, 1], np.float32))
