@@ -169,6 +169,9 @@ def parse():
     ap.add_argument("--W", type=int, default=4, help="pool entries expanded per search step")
     ap.add_argument("--no-tune", action="store_true", help="skip ann_autotune at L*")
     ap.add_argument("--modes", default="", help="comma list: only these entry modes (default: all)")
+    ap.add_argument("--precision", action="store_true",
+                    help="add the precision report (fp16 and int8 storage, with and without the exact "
+                         "rerank) to any workload")
     ap.add_argument("--hbkm", action="store_true",
                     help="hubs from hierarchical balanced k-means instead of flat k-means")
     ap.add_argument("--hbkm-lambda", type=float, default=1.0)
@@ -194,6 +197,8 @@ def parse():
         spec["hubs"] = args.hubs
     if args.no_learned:
         spec["learned"] = False
+    if args.precision:
+        spec["precision"] = True
     if not spec["learned"]:
         spec["n_train"] = 0
     if args.fixed_L:
