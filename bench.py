@@ -119,9 +119,9 @@ WORKLOADS = {
 # search launch, from an ncu capture of this bench's timed steps; it counts
 # only while the search kernel's sources are the ones it was taken on.
 MEASURED_TRAFFIC = {
-    # profiles/beam_search_shift1M.md: DRAM bytes read + written per headline
-    # launch, valid for these kernel sources, entry mode, L, batch and tuned
-    # sizes (spill_bits 0: the default for L)
+    # DRAM bytes read + written per headline launch, valid for these kernel
+    # sources, entry mode, L, batch and tuned sizes (spill_bits 0: the
+    # default for L)
     "shift": [
         dict(digest="d2ea997b04bffc6c", entry="exhaustive", L=93, nq=10_000, hash_bits=-1, stage_rows=8,
              team=4, spill_bits=0, bytes=3.576e9 + 0.730e9),

@@ -420,7 +420,9 @@ ann_status ann_select_entries(ann_index *idx, const void *d_queries, int64_t nq,
  *   ANN_ERR_CAPACITY before anything is queued; split them.
  *   The first call on a device looks up the array's device address on that
  *   device (a one-time set-up), so make the first call on each device before
- *   any stream capture.
+ *   any stream capture.  The address is kept until the process exits: after
+ *   a cudaDeviceReset by the host application it no longer names live
+ *   memory, so do not call this entry point on a device that was reset.
  *   All calls on a device share the one array: calls whose work overlaps on
  *   the GPU (for example on two streams) race and must be serialised by the
  *   caller.  Every word is written before it is read, so no clearing is needed.

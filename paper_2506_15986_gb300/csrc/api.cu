@@ -330,10 +330,13 @@ ann_status ann_load_index(const char *path, int device, ann_index **out)
         fclose(f);
         return ANN_ERR_FORMAT;
     }
+    // the limits ann_index_create enforces are checked here too, before the
+    // header's sizes drive any host allocation
     const int64_t rb = row_bytes(h.dtype, h.dim);
     bool sane = memcmp(h.magic, kMagic, 8) == 0 && h.version == kVersion &&
                 h.header_bytes == sizeof(FileHeader) && h.n >= 1 && h.n <= INT32_MAX && h.dim >= 1 &&
-                h.degree >= 1 && rb > 0 && h.bytes_base == static_cast<uint64_t>(h.n) * rb &&
+                h.degree >= 1 && h.degree <= ANN_MAX_STEP_CAND && rb > 0 && rb % 16 == 0 && rb <= 16384 &&
+                h.bytes_base == static_cast<uint64_t>(h.n) * rb &&
                 h.bytes_graph == static_cast<uint64_t>(h.n) * h.degree * 4 &&
                 h.bytes_f32 == ((h.flags & 1u) ? static_cast<uint64_t>(h.n) * h.dim * 4 : 0);
     if (!sane) {

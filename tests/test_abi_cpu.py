@@ -99,3 +99,17 @@ def test_index_file_errors_detected_on_host(lib, tmp_path):
     with open(p, "wb") as f:
         f.write(b"GATE")
     assert lib.ann_load_index(str(p).encode(), 0, ctypes.byref(out)) == ann.ERR_FORMAT
+
+
+def test_index_header_limits_checked_before_allocating(lib, tmp_path):
+    # a header whose sizes agree with each other but break the row limits of
+    # ann_index_create (rows a multiple of 16 bytes, at most 16 KiB; degree at
+    # most ANN_MAX_STEP_CAND) is a format error, found before the loader sizes
+    # any buffer from it (no data follows the header)
+    out = ctypes.c_void_p()
+    for n, dim, degree in ((4, 1 << 30, 4), (4, 17, 4), (4, 16, 129)):
+        hdr = struct.pack("<8sIIqiiiiiIQQQQ", b"GATEANN1", 1, 80, n, dim, degree, 0, 0, 0, 0,
+                          n * dim, n * degree * 4, 0, 0)
+        p = tmp_path / f"hdr_{dim}_{degree}.idx"
+        p.write_bytes(hdr)
+        assert lib.ann_load_index(str(p).encode(), 0, ctypes.byref(out)) == ann.ERR_FORMAT
