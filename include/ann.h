@@ -446,7 +446,7 @@ typedef struct ann_trainer ann_trainer;
 /*
  * Trainer of the two-tower model on one device.  Parameters start from the
  * given fp32 arrays (host or device; W1 [in_dim][256], b1 [256], W2 [256][64],
- * b2 [64], hub_emb [n_hubs][64]); Adam state starts at zero.
+ * b2 [64], hub_emb [n_hubs][64]); Adam state starts at zero.  n_hubs 2..65536.
  *   max_batch  largest batch (rows of scratch; the paper uses 8,192)
  *   tau        InfoNCE temperature; lr, beta1, beta2, eps: Adam
  * Every GEMM of a step runs on the tensor cores (BF16 operands, FP32
@@ -462,26 +462,33 @@ ann_status ann_trainer_free(ann_trainer *t);
 
 /*
  * One step on the batch of rows d_rows[0..nb) of d_queries (fp32, in_dim
- * columns, 16-byte aligned); d_mask holds one label row of n_hubs int8 per
- * query row (+1 positive, -1 negative, 0 unused).  Computes the loss and the
- * gradients of every parameter; applies the Adam update when apply_update is
- * non-zero.  loss_out (host, optional) receives the batch loss (blocking).
+ * columns, 16-byte aligned; d_rows NULL = rows 0..nb-1).  Labels: query row r
+ * lists M distinct hub indices d_cand[r*M + j] (-1 = empty slot) with labels
+ * d_labels[r*M + j] (+1 positive, -1 negative, 0 unused); every hub not
+ * listed for the row is a negative (a hub the label search did not reach
+ * from that query, Sec. 4.2).  A dense label matrix is the case M = n_hubs
+ * with d_cand[r*M + j] = j.  Computes the loss and the gradients of every
+ * parameter; applies the Adam update when apply_update is non-zero.
+ * loss_out (host, optional) receives the batch loss.
  * Sec. 4.3 Eq. loss and its gradient, Sec. 5.1 Adam. Blocking when loss_out
  * is given, else asynchronous; ANN_ERR_INVALID_ARG for a NULL or misaligned
- * input or nb out of range.
+ * input, M out of 1..n_hubs or nb out of range.
  */
 ann_status ann_trainer_step(ann_trainer *t, const float *d_queries, const int32_t *d_rows, int64_t nb,
-                            const int8_t *d_mask, int32_t apply_update, float *loss_out, void *stream);
+                            const int32_t *d_cand, const int8_t *d_labels, int32_t M, int32_t apply_update,
+                            float *loss_out, void *stream);
 
 /*
  * Epochs of steps over nt training queries; epoch e visits rows
  * d_order[e*nt .. e*nt+nt) (device, NULL = 0..nt-1) in batches of max_batch.
+ * d_cand, d_labels and M as for ann_trainer_step (nt*M entries each).
  * d_losses (device, optional) receives epochs * ceil(nt / max_batch) batch
  * losses.  Blocking.
  * Sec. 4.3 training with Sec. 5.1 Adam.
  */
-ann_status ann_trainer_fit(ann_trainer *t, const float *d_queries, int64_t nt, const int8_t *d_mask,
-                           const int32_t *d_order, int32_t epochs, float *d_losses, void *stream);
+ann_status ann_trainer_fit(ann_trainer *t, const float *d_queries, int64_t nt, const int32_t *d_cand,
+                           const int8_t *d_labels, int32_t M, const int32_t *d_order, int32_t epochs,
+                           float *d_losses, void *stream);
 
 /*
  * Copy the current parameters (gradients != 0: the last step's gradients).
@@ -635,13 +642,16 @@ ann_status ann_hub_costs(ann_index *idx, const void *d_queries, int64_t nq, cons
  * Label rule per query over its M searched hubs: best = argmin (evals, hops,
  * hub index) (-1 if none reached the target); m = min hops; label +1 if
  * hops <= m + t_pos, -1 if hops >= m + t_neg or never reached, 0 otherwise;
- * hubs not searched are -1; a query with no reached hub gets an all -1 row.
- *   d_mask out: nq*n_hubs int8; d_best out (optional): nq int32.  Asynchronous.
+ * a query with no reached hub gets -1 for every candidate.  The labels are
+ * aligned with the candidate list: d_labels[i*M + j] is the label of hub
+ * d_cand[i*M + j].  Hubs a query did not search are not listed and count as
+ * negatives wherever these labels are used (ann_trainer_step).
+ *   d_labels out: nq*M int8; d_best out (optional): nq int32.  Asynchronous;
+ *   ANN_ERR_INVALID_ARG for a NULL input or M < 1.
  * Sec. 4.2, Def. 4 and the labelling rule after it (t_pos, t_neg).
  */
 ann_status ann_hub_labels(const int32_t *d_evals, const int32_t *d_hops, const int32_t *d_cand, int64_t nq,
-                          int32_t M, int32_t n_hubs, int32_t t_pos, int32_t t_neg, int8_t *d_mask,
-                          int32_t *d_best, void *stream);
+                          int32_t M, int32_t t_pos, int32_t t_neg, int8_t *d_labels, int32_t *d_best, void *stream);
 
 /* ---- offline construction (GPU) ------------------------------------------ */
 

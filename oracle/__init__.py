@@ -334,6 +334,32 @@ def labels_from_costs(evals, hops, cand, n_hubs, t_pos=3, t_neg=15):
     return mask, best
 
 
+def labels_listed(evals, hops, cand, t_pos=3, t_neg=15):
+    """The label rule of ``labels_from_costs`` written per listed hub: for
+    query i, the label of its searched hub cand[i, j] (+1, -1 or 0, the same
+    rule), so that a hub not listed for a query is a negative (it was never
+    searched from that query).  Returns (labels int8 [nq, M], best int32 [nq]).
+    Sec. 4.2, Def. 4 and the per-query assignment after it."""
+    evals = np.asarray(evals, np.int64)
+    hops = np.asarray(hops, np.int64)
+    cand = np.asarray(cand, np.int64)
+    nq, M = cand.shape
+    lab = np.full((nq, M), -1, np.int8)
+    best = np.full(nq, -1, np.int32)
+    for i in range(nq):
+        reached = [j for j in range(M) if hops[i, j] < INT32_MAX]
+        if not reached:
+            continue
+        m = min(hops[i, j] for j in reached)
+        best[i] = cand[i, min(reached, key=lambda j: (evals[i, j], hops[i, j], cand[i, j]))]
+        for j in reached:
+            if hops[i, j] <= m + t_pos:
+                lab[i, j] = 1
+            elif hops[i, j] < m + t_neg:
+                lab[i, j] = 0
+    return lab, best
+
+
 def pruned_row(base, p, K, R, alpha=1.0):
     """Steps 1-2 of the graph builder (Sec. 2.1, Def. 1) for the single node p:
     its K exact nearest other nodes by (dist, id), then relative-neighbourhood

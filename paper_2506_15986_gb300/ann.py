@@ -92,8 +92,8 @@ def load_library(path: str | None = None):
         "ann_trainer_create": ([i32, i32, i32, _p, _p, _p, _p, _p, i64, _c.c_float, _c.c_float,
                                 _c.c_float, _c.c_float, _c.c_float, pp], i32),
         "ann_trainer_free": ([_p], i32),
-        "ann_trainer_step": ([_p, _p, _p, i64, _p, i32, _c.POINTER(_c.c_float), _p], i32),
-        "ann_trainer_fit": ([_p, _p, i64, _p, _p, i32, _p, _p], i32),
+        "ann_trainer_step": ([_p, _p, _p, i64, _p, _p, i32, i32, _c.POINTER(_c.c_float), _p], i32),
+        "ann_trainer_fit": ([_p, _p, i64, _p, _p, i32, _p, i32, _p, _p], i32),
         "ann_trainer_get": ([_p, _p, _p, _p, _p, _p, i32], i32),
         "ann_trainer_attach": ([_p, _p, _p, i32, _p], i32),
         "ann_adam_update": ([_p, _p, _p, _p, i64, i64, _c.c_float, _c.c_float, _c.c_float,
@@ -107,7 +107,7 @@ def load_library(path: str | None = None):
         "ann_trainer_set_fusion": ([_p, _p, _p, i32, i32, i32, i32, _p, _p, _p, _p], i32),
         "ann_trainer_get_fusion": ([_p, _p, _p, _p, _p, i32], i32),
         "ann_hub_costs": ([_p, _p, i64, _p, _p, i32, _p, i32, i32, _p, _p, _p], i32),
-        "ann_hub_labels": ([_p, _p, _p, i64, i32, i32, i32, i32, _p, _p, _p], i32),
+        "ann_hub_labels": ([_p, _p, _p, i64, i32, i32, i32, _p, _p, _p], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -311,18 +311,20 @@ def ann_trainer_free(t):
     _check(load_library().ann_trainer_free(t), "ann_trainer_free")
 
 
-def ann_trainer_step(t, queries, rows, nb, mask, apply_update=True, stream=None):
-    """One step; returns the batch loss (blocking)."""
+def ann_trainer_step(t, queries, rows, nb, cand, labels, M, apply_update=True, stream=None):
+    """One step; returns the batch loss (blocking).  cand / labels: M listed
+    hubs per query row and their labels (+1, -1, 0); unlisted hubs are
+    negatives."""
     loss = _c.c_float(0.0)
-    _check(load_library().ann_trainer_step(t, _ptr(queries), _ptr(rows), int(nb), _ptr(mask),
-                                           int(bool(apply_update)), ctypes.byref(loss),
+    _check(load_library().ann_trainer_step(t, _ptr(queries), _ptr(rows), int(nb), _ptr(cand), _ptr(labels),
+                                           int(M), int(bool(apply_update)), ctypes.byref(loss),
                                            _stream(stream)), "ann_trainer_step")
     return loss.value
 
 
-def ann_trainer_fit(t, queries, nt, mask, order, epochs, losses=None, stream=None):
-    _check(load_library().ann_trainer_fit(t, _ptr(queries), int(nt), _ptr(mask), _ptr(order),
-                                          int(epochs), _ptr(losses), _stream(stream)),
+def ann_trainer_fit(t, queries, nt, cand, labels, M, order, epochs, losses=None, stream=None):
+    _check(load_library().ann_trainer_fit(t, _ptr(queries), int(nt), _ptr(cand), _ptr(labels), int(M),
+                                          _ptr(order), int(epochs), _ptr(losses), _stream(stream)),
            "ann_trainer_fit")
 
 
@@ -369,10 +371,12 @@ def ann_hub_costs(h, queries, nq, targets, cand, M, hub_nodes, L, evals, hops, W
                                         _ptr(hops), _stream(stream)), "ann_hub_costs")
 
 
-def ann_hub_labels(evals, hops, cand, nq, M, n_hubs, t_pos, t_neg, mask, best=None, stream=None):
+def ann_hub_labels(evals, hops, cand, nq, M, t_pos, t_neg, labels, best=None, stream=None):
+    """Label rule per query over its M searched hubs: labels (nq x M int8)
+    aligned with cand; unlisted hubs count as negatives."""
     _check(load_library().ann_hub_labels(_ptr(evals), _ptr(hops), _ptr(cand), int(nq), int(M),
-                                         int(n_hubs), int(t_pos), int(t_neg), _ptr(mask),
-                                         _ptr(best), _stream(stream)), "ann_hub_labels")
+                                         int(t_pos), int(t_neg), _ptr(labels), _ptr(best), _stream(stream)),
+           "ann_hub_labels")
 
 
 def ann_select_entry_noalloc(h, queries, nq, entry_out, qhat_out=None, stream=None):

@@ -97,16 +97,15 @@ __global__ void expand_entries(const int32_t *cand, int64_t count, const int32_t
         entries[i] = hub_nodes[cand[i]];
 }
 
-// one thread per query: the label rule over its M searched hubs
+// one thread per query: the label rule over its M searched hubs, written as
+// labels aligned with the candidate list (hubs not listed are negatives)
 __global__ void label_rule_kernel(const int32_t *evals, const int32_t *hops, const int32_t *cand, int64_t nq, int M,
-                                  int H, int t_pos, int t_neg, int8_t *mask, int32_t *best)
+                                  int t_pos, int t_neg, int8_t *lab, int32_t *best)
 {
     const int64_t q = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
     if (q >= nq)
         return;
-    int8_t *row = mask + q * H;
-    for (int h = 0; h < H; ++h)
-        row[h] = -1;  // not searched: negative
+    int8_t *row = lab + q * M;
     const int32_t *ev = evals + q * M, *hp = hops + q * M, *cd = cand + q * M;
     int mh = INT32_MAX, be = -1;
     for (int j = 0; j < M; ++j) {
@@ -118,19 +117,17 @@ __global__ void label_rule_kernel(const int32_t *evals, const int32_t *hops, con
     }
     if (best)
         best[q] = be >= 0 ? cd[be] : -1;
-    if (be < 0)
-        return;
     for (int j = 0; j < M; ++j) {
         int8_t v;
-        if (hp[j] == INT32_MAX)
-            v = -1;
+        if (be < 0 || hp[j] == INT32_MAX)
+            v = -1;  // no hub reached the target, or this one never did
         else if (hp[j] <= mh + t_pos)
             v = 1;
         else if (hp[j] >= mh + t_neg)
             v = -1;
         else
             v = 0;
-        row[cd[j]] = v;
+        row[j] = v;
     }
 }
 
@@ -338,14 +335,14 @@ ann_status ann_hub_costs(ann_index *idx, const void *d_queries, int64_t nq, cons
 }
 
 ann_status ann_hub_labels(const int32_t *d_evals, const int32_t *d_hops, const int32_t *d_cand, int64_t nq, int32_t M,
-                          int32_t n_hubs, int32_t t_pos, int32_t t_neg, int8_t *d_mask, int32_t *d_best, void *stream)
+                          int32_t t_pos, int32_t t_neg, int8_t *d_labels, int32_t *d_best, void *stream)
 {
-    if (!d_evals || !d_hops || !d_cand || !d_mask || nq < 0 || M < 1 || n_hubs < 1 || t_pos < 0 || t_neg < 0)
+    if (!d_evals || !d_hops || !d_cand || !d_labels || nq < 0 || M < 1 || t_pos < 0 || t_neg < 0)
         return ANN_ERR_INVALID_ARG;
     if (nq == 0)
         return ANN_OK;
     label_rule_kernel<<<static_cast<unsigned>((nq + 127) / 128), 128, 0, static_cast<cudaStream_t>(stream)>>>(
-        d_evals, d_hops, d_cand, nq, M, n_hubs, t_pos, t_neg, d_mask, d_best);
+        d_evals, d_hops, d_cand, nq, M, t_pos, t_neg, d_labels, d_best);
     return cuda_status(cudaGetLastError());
 }
 

@@ -11,18 +11,20 @@
 //   - the candidate pool: L 64-bit (distance, id, expanded) keys kept sorted;
 //     new candidates are sorted by a warp-shuffle bitonic network and merged
 //     in by rank (merge path);
-//   - the visited set: an open-addressing hash table (linear probing, key
-//     id+1, 0 = empty).  When it would pass 3/4 load, its entries move to a
-//     per-team table in global scratch that takes every later insert, so
-//     the set stays exact; that one hands over in turn to a four times
-//     larger global table, and only when the last would pass 3/4 load does
-//     the query fail with a capacity status.
-// Semantics follow the sorted-pool reading of Algorithm 1: single entry, a
-// node is visited when its distance is computed, a step expands the first W
-// unexpanded pool entries, the pool is truncated to L, the search stops when
-// no unexpanded entry is left.  Results are independent of the order in which
-// the lanes of a step insert, because the pool is the L smallest keys of the
-// union under a total order.
+//   - optionally, the first level of the visited set (hash_bits > 0).
+// The visited set is an exact open-addressing hash (linear probing, key id+1,
+// 0 = empty) with up to three levels: the optional shared-memory table, a
+// per-team table in global scratch (2^spill_bits slots), and one four times
+// larger.  A level that would pass 3/4 load hands its keys to the next one,
+// which takes every later insert; only past the last does the query fail
+// with a capacity status.  Without a shared table (hash_bits = -1, what the
+// tuned configurations use) the set starts in the first global table.
+// Semantics follow the sorted-pool reading of Algorithm 1: a seed set (one
+// entry by default), a node is visited when its distance is computed, a step
+// expands the first W unexpanded pool entries, the pool is truncated to L,
+// the search stops when no unexpanded entry is left.  Results are
+// independent of the order in which the lanes of a step insert, because the
+// pool is the L smallest keys of the union under a total order.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -68,6 +70,7 @@ struct SearchArgs {
     int off_sel, off_q, off_stage, off_pool, off_ptop, off_cbuf, off_hash, per_warp;
     int stage_rows, stage_stride;
     int team_lg;  // log2 of the lanes computing one distance
+    int cpl;      // 16-byte chunks of a row per lane when they divide evenly into 1, 2, 4 or 8, else 0
 };
 
 __device__ __forceinline__ uint32_t hash_slot(uint32_t key, int bits)
@@ -184,18 +187,20 @@ __device__ __forceinline__ void migrate_keys(const uint32_t *src, int sbits, boo
 // Distance of one staged row to the query, computed by a team of G lanes
 // (G a power of two <= 32; sub = lane % G takes the row's 16-byte chunks sub,
 // sub+G, ...) and combined with log2(G) xor-shuffles inside the team; every
-// lane of the team returns the order-preserving key bits.  The whole warp
+// lane of the team returns the order-preserving key bits.  CPL > 0: the row
+// has exactly CPL * G chunks, so the chunk loop is unrolled and its shared-
+// memory loads issue back to back (CPL = 0: any chunk count).  The whole warp
 // must call it.
-template <int DT, int MT>
+template <int DT, int MT, int CPL>
 __device__ __forceinline__ uint32_t group_distance(const uint8_t *row, const uint8_t *q, int rowbytes, int sub,
                                                    int G)
 {
-    const int chunks = rowbytes / 16;
+    const int chunks = CPL > 0 ? CPL * G : rowbytes / 16;
     if constexpr (DT == ANN_U8) {
         const uint4 *x4 = reinterpret_cast<const uint4 *>(row);
         const uint4 *q4 = reinterpret_cast<const uint4 *>(q);
         uint32_t acc = 0;
-        for (int c = sub; c < chunks; c += G) {
+        auto chunk = [&](int c) {
             const uint4 x = x4[c], y = q4[c];
             uint32_t d;
             d = __vabsdiffu4(x.x, y.x);
@@ -206,6 +211,14 @@ __device__ __forceinline__ uint32_t group_distance(const uint8_t *row, const uin
             acc = __dp4a(d, d, acc);
             d = __vabsdiffu4(x.w, y.w);
             acc = __dp4a(d, d, acc);
+        };
+        if constexpr (CPL > 0) {
+#pragma unroll
+            for (int i = 0; i < CPL; ++i)
+                chunk(sub + i * G);
+        } else {
+            for (int c = sub; c < chunks; c += G)
+                chunk(c);
         }
         for (int o = G >> 1; o > 0; o >>= 1)
             acc += __shfl_xor_sync(kFull, acc, o);
@@ -251,9 +264,6 @@ __device__ __forceinline__ uint32_t group_distance(const uint8_t *row, const uin
         return f32_to_ord(s);
     } else {
         const float4 *q4 = reinterpret_cast<const float4 *>(q);
-        // two FP32 accumulators (even and odd coordinates) held as one packed
-        // pair: each f32x2 operation rounds both halves exactly as the scalar
-        // operations would, at half the instruction count
         // four FP32 accumulators (coordinates 4c+0..3) held as two packed
         // pairs: each f32x2 operation rounds both halves exactly as the scalar
         // operations would, at half the instruction count, and the two pairs
@@ -277,16 +287,12 @@ __device__ __forceinline__ uint32_t group_distance(const uint8_t *row, const uin
                     : "+l"(acc), "+l"(acc2)
                     : "f"(x0), "f"(x1), "f"(x2), "f"(x3), "f"(y.x), "f"(y.y), "f"(y.z), "f"(y.w));
         };
-        if constexpr (DT == ANN_F32) {
-            const float4 *x4 = reinterpret_cast<const float4 *>(row);
-            for (int c = sub; c < chunks; c += G) {
-                const float4 x = x4[c];
+        auto chunk = [&](int c) {
+            if constexpr (DT == ANN_F32) {
+                const float4 x = reinterpret_cast<const float4 *>(row)[c];
                 acc4(x.x, x.y, x.z, x.w, q4[c]);
-            }
-        } else {
-            const uint4 *x8 = reinterpret_cast<const uint4 *>(row);
-            for (int c = sub; c < chunks; c += G) {
-                const uint4 x = x8[c];
+            } else {
+                const uint4 x = reinterpret_cast<const uint4 *>(row)[c];
                 float2 f0, f1, f2, f3;
                 if constexpr (DT == ANN_F16) {
                     f0 = __half22float2(*reinterpret_cast<const __half2 *>(&x.x));
@@ -302,6 +308,14 @@ __device__ __forceinline__ uint32_t group_distance(const uint8_t *row, const uin
                 acc4(f0.x, f0.y, f1.x, f1.y, q4[2 * c]);
                 acc4(f2.x, f2.y, f3.x, f3.y, q4[2 * c + 1]);
             }
+        };
+        if constexpr (CPL > 0) {
+#pragma unroll
+            for (int i = 0; i < CPL; ++i)
+                chunk(sub + i * G);
+        } else {
+            for (int c = sub; c < chunks; c += G)
+                chunk(c);
         }
         float s = (__uint_as_float(static_cast<uint32_t>(acc)) + __uint_as_float(static_cast<uint32_t>(acc >> 32))) +
                   (__uint_as_float(static_cast<uint32_t>(acc2)) + __uint_as_float(static_cast<uint32_t>(acc2 >> 32)));
@@ -313,8 +327,26 @@ __device__ __forceinline__ uint32_t group_distance(const uint8_t *row, const uin
     }
 }
 
+// group_distance with the chunk count per lane picked at run time: cpl is
+// uniform over the launch (0 = the general loop).
 template <int DT, int MT>
-__global__ void __launch_bounds__(32 * kMaxSearchWarps) beam_search_kernel(const SearchArgs a)
+__device__ __forceinline__ uint32_t row_distance(const uint8_t *row, const uint8_t *q, int rowbytes, int sub, int G,
+                                                 int cpl)
+{
+    if constexpr (DT != ANN_I8S) {
+        switch (cpl) {
+        case 8: return group_distance<DT, MT, 8>(row, q, rowbytes, sub, G);
+        case 4: return group_distance<DT, MT, 4>(row, q, rowbytes, sub, G);
+        case 2: return group_distance<DT, MT, 2>(row, q, rowbytes, sub, G);
+        case 1: return group_distance<DT, MT, 1>(row, q, rowbytes, sub, G);
+        default: break;
+        }
+    }
+    return group_distance<DT, MT, 0>(row, q, rowbytes, sub, G);
+}
+
+template <int DT, int MT>
+__global__ void __launch_bounds__(32 * kMaxSearchWarps, 16) beam_search_kernel(const SearchArgs a)
 {
     extern __shared__ __align__(128) uint8_t smem[];
     const int lane = threadIdx.x & 31;
@@ -440,8 +472,8 @@ __global__ void __launch_bounds__(32 * kMaxSearchWarps) beam_search_kernel(const
                     for (int r0 = 0; r0 < ch; r0 += 32 >> a.team_lg) {
                         const int r = r0 + (lane >> a.team_lg);
                         const int sub = lane & ((1 << a.team_lg) - 1);
-                        const uint32_t bits = group_distance<DT, MT>(stage + min(r, ch - 1) * a.stage_stride,
-                                                                     qbuf, a.rowbytes, sub, 1 << a.team_lg);
+                        const uint32_t bits = row_distance<DT, MT>(stage + min(r, ch - 1) * a.stage_stride, qbuf,
+                                                                   a.rowbytes, sub, 1 << a.team_lg, a.cpl);
                         if (r < ch && sub == 0)
                             cbuf[c0 + r] = make_key(bits, key_id(cbuf[c0 + r]));
                     }
@@ -930,6 +962,11 @@ ann_status launch_search(ann_index *idx, const SearchLaunch &L, cudaStream_t s)
         while (s16 % G != 0 || ((s16 / G) & 1) == 0)
             ++s16;
     a.stage_stride = s16 * 16;
+    a.cpl = 0;
+    if (idx->dtype != ANN_I8S && chunks % G == 0) {
+        const int c = chunks / G;
+        a.cpl = (c == 1 || c == 2 || c == 4 || c == 8) ? c : 0;
+    }
     // Most steps find far fewer new neighbours than W * R (about 30 % of
     // them), so a small staging area filled in rounds keeps shared memory per
     // team small (more teams per SM); at most 48 KB staged at once, which also

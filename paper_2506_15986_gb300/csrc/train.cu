@@ -33,6 +33,9 @@
 namespace ann {
 namespace {
 
+// hubs a trainer takes: one InfoNCE block holds a row's labels in shared memory
+constexpr int kMaxTrainHubs = 65536;
+
 // ---- generic tensor-core GEMM ------------------------------------------------
 
 enum Epi { EPI_STORE = 0, EPI_RELU_MASK = 1 };
@@ -173,53 +176,80 @@ __global__ void transpose_bf16(const Operand src, int64_t rows, int64_t cols, __
     }
 }
 
-// Per batch row: masked multi-positive InfoNCE over the labelled hubs.
-// Writes the row loss, a validity flag (|P| > 0) and the unscaled gradient
-// softmax_{P u N}(S) - 1[P]/|P| (0 outside P u N and on invalid rows).
-__global__ void infonce_kernel(const float *S, int64_t B, int H, const int8_t *mask, const int32_t *rowmap,
-                               float *dS, float *row_loss, int *valid)
+// Sum (or maximum) over the block of one value per thread; every thread gets
+// the result.  red holds 32 slots; blockDim.x is a multiple of 32.
+template <bool MAX>
+__device__ __forceinline__ float block_reduce(float v, float *red)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t r = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5;
-    if (r >= B)
-        return;
-    const int64_t mr = rowmap ? rowmap[r] : r;
-    const int8_t *m = mask + mr * H;
-    const float *s = S + r * H;
-    float mx = -INFINITY;
-    int npos = 0;
-    for (int c = lane; c < H; c += 32) {
-        if (m[c] != 0)
-            mx = fmaxf(mx, s[c]);
-        npos += m[c] > 0;
-    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        mx = fmaxf(mx, __shfl_xor_sync(kFull, mx, o));
-        npos += __shfl_xor_sync(kFull, npos, o);
+        const float w = __shfl_xor_sync(kFull, v, o);
+        v = MAX ? fmaxf(v, w) : v + w;
     }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();  // red is free again
+    if (lane == 0)
+        red[wid] = v;
+    __syncthreads();
+    v = lane < nw ? red[lane] : (MAX ? -INFINITY : 0.f);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float w = __shfl_xor_sync(kFull, v, o);
+        v = MAX ? fmaxf(v, w) : v + w;
+    }
+    return v;
+}
+
+// One block per batch row: masked multi-positive InfoNCE over the labelled
+// hubs.  The row's labels come as its M listed hubs (cand, lab); every hub
+// not listed is a negative, so the row's H labels are first laid out in
+// shared memory (all -1, then the listed ones).  Writes the row loss, a
+// validity flag (|P| > 0) and the unscaled gradient softmax_{P u N}(S) -
+// 1[P]/|P| (0 outside P u N and on invalid rows).
+__global__ void infonce_kernel(const float *S, int64_t B, int H, const int32_t *cand, const int8_t *lab, int M,
+                               const int32_t *rowmap, float *dS, float *row_loss, int *valid)
+{
+    extern __shared__ int8_t lrow[];
+    __shared__ float red[32];
+    const int64_t r = blockIdx.x;
+    const int64_t mr = rowmap ? rowmap[r] : r;
+    for (int c = threadIdx.x; c < H; c += blockDim.x)
+        lrow[c] = -1;
+    __syncthreads();
+    for (int j = threadIdx.x; j < M; j += blockDim.x) {
+        const int32_t h = cand[mr * M + j];
+        if (h >= 0 && h < H)
+            lrow[h] = lab[mr * M + j];
+    }
+    __syncthreads();
+    const float *s = S + r * H;
+    float mx = -INFINITY, np = 0.f;
+    for (int c = threadIdx.x; c < H; c += blockDim.x) {
+        if (lrow[c] != 0)
+            mx = fmaxf(mx, s[c]);
+        np += lrow[c] > 0 ? 1.f : 0.f;
+    }
+    mx = block_reduce<true>(mx, red);
+    const int npos = static_cast<int>(block_reduce<false>(np, red));
     float z = 0.f, sp = 0.f;
-    for (int c = lane; c < H; c += 32) {
-        if (m[c] != 0)
+    for (int c = threadIdx.x; c < H; c += blockDim.x) {
+        if (lrow[c] != 0)
             z += expf(s[c] - mx);
-        if (m[c] > 0)
+        if (lrow[c] > 0)
             sp += s[c];
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        z += __shfl_xor_sync(kFull, z, o);
-        sp += __shfl_xor_sync(kFull, sp, o);
-    }
+    z = block_reduce<false>(z, red);
+    sp = block_reduce<false>(sp, red);
     const float lse = mx + logf(z);
     const bool ok = npos > 0;
     const float inv_np = ok ? 1.f / static_cast<float>(npos) : 0.f;
-    for (int c = lane; c < H; c += 32) {
+    for (int c = threadIdx.x; c < H; c += blockDim.x) {
         float g = 0.f;
-        if (ok && m[c] != 0)
-            g = expf(s[c] - lse) - (m[c] > 0 ? inv_np : 0.f);
+        if (ok && lrow[c] != 0)
+            g = expf(s[c] - lse) - (lrow[c] > 0 ? inv_np : 0.f);
         dS[r * H + c] = g;
     }
-    if (lane == 0) {
+    if (threadIdx.x == 0) {
         row_loss[r] = ok ? -(sp - npos * lse) * inv_np : 0.f;
         valid[r] = ok ? 1 : 0;
     }
@@ -397,7 +427,7 @@ Offs offsets(int in_dim, int H)
 
 // forward + loss + backward for one batch; grads written to t->grads
 ann_status trainer_grads(ann_trainer *t, const float *d_queries, const int32_t *rows, int64_t B,
-                         const int8_t *d_mask, cudaStream_t s)
+                         const int32_t *d_cand, const int8_t *d_lab, int n_listed, cudaStream_t s)
 {
     ann_entry_model &M = t->model;
     const Offs o = offsets(t->in_dim, t->H);
@@ -432,7 +462,8 @@ ann_status trainer_grads(ann_trainer *t, const float *d_queries, const int32_t *
     g.ldo = H;
     if ((st = gemm<128>(g, s)) != ANN_OK)
         return st;
-    infonce_kernel<<<blocks_for(B * 32, 256), 256, 0, s>>>(t->S, B, H, d_mask, rows, t->dS, t->row_loss, t->valid);
+    infonce_kernel<<<static_cast<unsigned>(B), 256, H, s>>>(t->S, B, H, d_cand, d_lab, n_listed, rows, t->dS,
+                                                             t->row_loss, t->valid);
     finalize_loss_kernel<<<1, 256, 0, s>>>(t->row_loss, t->valid, B, t->tau, t->loss, t->scale);
     // dq_hat = scale * dS e_hat  (B x 64, K = H)
     transpose_bf16<<<dim3(blocks_for(64, 32), blocks_for(H, 32)), dim3(32, 8), 0, s>>>(
@@ -529,6 +560,7 @@ ann_status ann_trainer_create(int device, int32_t in_dim, int32_t n_hubs, const 
                               float tau, float lr, float beta1, float beta2, float eps, ann_trainer **out)
 {
     if (!out || !W1 || !b1 || !W2 || !b2 || !hub_emb || in_dim < 1 || in_dim > 512 || n_hubs < 2 ||
+        n_hubs > kMaxTrainHubs ||
         max_batch < 1 || max_batch > (1 << 20) || !(tau > 0.f) || !(lr > 0.f) || !(beta1 >= 0.f && beta1 < 1.f) ||
         !(beta2 >= 0.f && beta2 < 1.f) || !(eps > 0.f))
         return ANN_ERR_INVALID_ARG;
@@ -536,6 +568,8 @@ ann_status ann_trainer_create(int device, int32_t in_dim, int32_t n_hubs, const 
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
         return ANN_ERR_CUDA;
     cudaSetDevice(device);
+    if (cudaFuncSetAttribute(infonce_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, n_hubs) != cudaSuccess)
+        return ANN_ERR_CUDA;
     ann_trainer *t = new (std::nothrow) ann_trainer();
     if (!t)
         return ANN_ERR_OOM;
@@ -627,14 +661,15 @@ ann_status ann_trainer_free(ann_trainer *t)
 }
 
 ann_status ann_trainer_step(ann_trainer *t, const float *d_queries, const int32_t *d_rows, int64_t nb,
-                            const int8_t *d_mask, int32_t apply_update, float *loss_out, void *stream)
+                            const int32_t *d_cand, const int8_t *d_labels, int32_t M, int32_t apply_update,
+                            float *loss_out, void *stream)
 {
-    if (!t || !d_queries || !d_mask || nb < 1 || nb > t->batch ||
+    if (!t || !d_queries || !d_cand || !d_labels || M < 1 || M > t->H || nb < 1 || nb > t->batch ||
         (reinterpret_cast<uintptr_t>(d_queries) & 15))
         return ANN_ERR_INVALID_ARG;
     cudaSetDevice(t->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    ann_status st = trainer_grads(t, d_queries, d_rows, nb, d_mask, s);
+    ann_status st = trainer_grads(t, d_queries, d_rows, nb, d_cand, d_labels, M, s);
     if (st != ANN_OK)
         return st;
     if (apply_update) {
@@ -684,10 +719,12 @@ ann_status ann_trainer_get(const ann_trainer *t, float *W1, float *b1, float *W2
     return cuda_status(e);
 }
 
-ann_status ann_trainer_fit(ann_trainer *t, const float *d_queries, int64_t nt, const int8_t *d_mask,
-                           const int32_t *d_order, int32_t epochs, float *d_losses, void *stream)
+ann_status ann_trainer_fit(ann_trainer *t, const float *d_queries, int64_t nt, const int32_t *d_cand,
+                           const int8_t *d_labels, int32_t M, const int32_t *d_order, int32_t epochs,
+                           float *d_losses, void *stream)
 {
-    if (!t || !d_queries || !d_mask || nt < 1 || epochs < 0 || (reinterpret_cast<uintptr_t>(d_queries) & 15))
+    if (!t || !d_queries || !d_cand || !d_labels || M < 1 || M > t->H || nt < 1 || epochs < 0 ||
+        (reinterpret_cast<uintptr_t>(d_queries) & 15))
         return ANN_ERR_INVALID_ARG;
     cudaSetDevice(t->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -709,7 +746,7 @@ ann_status ann_trainer_fit(ann_trainer *t, const float *d_queries, int64_t nt, c
         const int32_t *ord = d_order ? d_order + static_cast<int64_t>(ep) * nt : iota;
         for (int64_t i = 0; i < spe && st == ANN_OK; ++i) {
             const int64_t nb = std::min<int64_t>(t->batch, nt - i * t->batch);
-            st = trainer_grads(t, d_queries, ord + i * t->batch, nb, d_mask, s);
+            st = trainer_grads(t, d_queries, ord + i * t->batch, nb, d_cand, d_labels, M, s);
             if (st != ANN_OK)
                 break;
             adam_all(t, s);

@@ -33,3 +33,11 @@ def search(h, queries, k, L, W=1, entries=None, hash_bits=0, ks=None, Ls=None, t
     st = ann.ann_sync_status(h)
     return ids.cpu().numpy(), dists.cpu().numpy(), stats[:, 0].cpu().numpy(), \
         stats[:, 1].cpu().numpy(), st
+
+
+def dense_as_listed(mask):
+    """A dense nq x H label matrix (numpy int8) in the trainer's listed form:
+    every hub listed for every query.  Returns (cand, labels, M) on cuda:0."""
+    nq, H = mask.shape
+    cand = torch.arange(H, dtype=torch.int32, device=DEV).repeat(nq, 1).contiguous()
+    return cand, torch.from_numpy(np.ascontiguousarray(mask, np.int8)).to(DEV), H

@@ -2,12 +2,20 @@
 
 The paper fixes no precision.  The tensor-core path takes its GEMM operands in
 BF16 (queries, W1, the hidden layer, W2, normalised hub embeddings) and
-accumulates in FP32; the oracle is fed the same BF16-rounded operands and
-computes in float64, so the remaining difference is FP32 accumulation:
-|q_hat_gpu - q_hat_oracle| <= 2e-4 per component.  Choices decided by floating
-point (argmax over hubs, the hub-graph search) are compared by the oracle's
-score of the GPU's choice: within 1e-4 of the best, and equal choices for
->= 99% of queries."""
+accumulates in FP32.  Two comparisons follow from that:
+
+* against the oracle fed the same BF16-rounded operands (float64 arithmetic),
+  the difference is FP32 accumulation plus the rare hidden unit whose BF16
+  rounding falls the other way in the two precisions (the bars are derived in
+  test_tower_matches_oracle);
+* against the unrounded float64 tower, q_hat must stay within a first-order
+  bound on what the BF16 roundings can move it, computed per query from the
+  operands (test_tower_within_bf16_bound_of_float64_model).
+
+Choices decided by floating point (argmax over hubs, the hub-graph search) are
+made by the oracle from its own q_hat and compared by the oracle's score of
+the GPU's choice, within a bound derived from the two q_hat vectors, with
+equal choices for >= 99% of queries."""
 import numpy as np
 import pytest
 
@@ -88,15 +96,59 @@ def test_tower_matches_oracle(setup):
     np.testing.assert_allclose(np.linalg.norm(qh, axis=1), 1.0, atol=1e-5)
 
 
+def _bf16_bound(q, W):
+    """Per-query first-order bound on ||q_hat - q_hat_exact||_2 when the
+    inputs, W1, the hidden layer and W2 are each rounded to BF16 (unit
+    roundoff u = 2^-9, every rounding |r(x) - x| <= u |x|) and the two GEMMs
+    accumulate in FP32 (at most K * 2^-24 of the sum of |products| each):
+      |dZ1_j| <= sum_i |q_i W1_ij| (2u + u^2 + (d+1) 2^-24) = B1_j
+      |dA1_j| <= B1_j + u (|A1_j| + B1_j) = B2_j        (ReLU is 1-Lipschitz)
+      |dZ2_k| <= sum_j (B2_j (1+u) + u |A1_j|) |W2_jk| + 257 * 2^-24 sum_j |A1_j W2_jk| = B3_k
+      ||d q_hat|| <= 2 ||B3|| / ||Z2||                    (normalisation)"""
+    W1, b1, W2, b2, _ = W
+    u, e32 = 2.0 ** -9, 2.0 ** -24
+    X = np.asarray(q, np.float64)
+    A = np.abs(X) @ np.abs(W1.astype(np.float64))
+    Z1 = X @ W1.astype(np.float64) + b1
+    A1 = np.maximum(Z1, 0.0)
+    d = X.shape[1]
+    B1 = A * (2 * u + u * u + (d + 1) * e32)
+    B2 = B1 + u * (np.abs(A1) + B1)
+    aW2 = np.abs(W2.astype(np.float64))
+    B3 = (B2 * (1 + u) + u * np.abs(A1)) @ aW2 + 257 * e32 * (np.abs(A1) @ aW2)
+    Z2 = A1 @ W2.astype(np.float64) + b2
+    return 2 * np.linalg.norm(B3, axis=1) / np.linalg.norm(Z2, axis=1)
+
+
+def test_tower_within_bf16_bound_of_float64_model(setup):
+    # the q_hat a user gets, against the unrounded float64 model
+    _, qh = _select(setup, ann.ENTRY_LEARNED_EXHAUSTIVE)
+    W1, b1, W2, b2, _ = setup["W"]
+    exact, _ = ot.tower_forward(setup["q"], W1.astype(np.float64), b1.astype(np.float64),
+                                W2.astype(np.float64), b2.astype(np.float64))
+    err = np.linalg.norm(qh - exact, axis=1)
+    bound = _bf16_bound(setup["q"], setup["W"])
+    assert (err <= bound).all(), (err / bound).max()
+    # the bound is worst case; the typical error is far below it
+    assert np.median(err / bound) < 0.2
+
+
 def test_exhaustive_argmax_matches_oracle(setup):
     ent, qh = _select(setup, ann.ENTRY_LEARNED_EXHAUSTIVE)
     Eb = _eb(setup["W"][4])
-    S = ot.bf16_round(qh) @ Eb.T  # the operands the tensor cores see
+    # the oracle's own choice: argmax over its own (BF16-rounded) q_hat
+    ref_q = ot.bf16_round(_oracle_qhat(setup["q"], setup["W"]))
+    S = ref_q @ Eb.T
     hub_of = {int(n): i for i, n in enumerate(setup["hub_nodes"])}
     chosen = np.array([hub_of[int(e)] for e in ent])
     best = S.max(1)
     got = S[np.arange(len(S)), chosen]
-    assert (best - got).max() <= 1e-4
+    # a GPU choice that maximises its own scores loses at most twice the
+    # largest score difference between the two q_hat vectors (|ds| <=
+    # ||dq|| * max ||e_v||) plus twice the FP32 error of a 64-term dot
+    # product of unit vectors (64 * 2^-24 < 5e-6)
+    dq = np.linalg.norm(ot.bf16_round(qh) - ref_q, axis=1) * np.linalg.norm(Eb, axis=1).max()
+    assert (best - got <= 2 * dq + 1e-5).all(), (best - got - 2 * dq).max()
     assert (chosen == S.argmax(1)).mean() >= 0.99
 
 

@@ -45,12 +45,12 @@ def test_hub_costs_and_labels_bit_exact(c1):
                       ev, hp)
     assert ann.ann_sync_status(c1["h"]) == ann.OK
     assert np.array_equal(ev.cpu().numpy(), ev_o) and np.array_equal(hp.cpu().numpy(), hp_o)
-    mask_o, best_o = oracle.labels_from_costs(ev_o, hp_o, cand, 50, t_pos=3, t_neg=15)
-    mask = torch.empty((len(q), 50), dtype=torch.int8, device=DEV)
+    lab_o, best_o = oracle.labels_listed(ev_o, hp_o, cand, t_pos=3, t_neg=15)
+    lab = torch.empty((len(q), M), dtype=torch.int8, device=DEV)
     best = torch.empty(len(q), dtype=torch.int32, device=DEV)
-    ann.ann_hub_labels(ev, hp, torch.from_numpy(cand).to(DEV), len(q), M, 50, 3, 15, mask, best)
+    ann.ann_hub_labels(ev, hp, torch.from_numpy(cand).to(DEV), len(q), M, 3, 15, lab, best)
     torch.cuda.synchronize()
-    assert np.array_equal(mask.cpu().numpy(), mask_o)
+    assert np.array_equal(lab.cpu().numpy(), lab_o)
     assert np.array_equal(best.cpu().numpy(), best_o)
 
 
@@ -59,13 +59,14 @@ def test_label_rule_edge_rows():
     cand = np.array([[4, 0, 1, 2, 3], [0, 1, 2, 3, 4]], np.int32)
     ev = np.array([[50, 40, 40, I, 300], [I, I, I, I, I]], np.int32)
     hp = np.array([[6, 5, 4, I, 12], [I, I, I, I, I]], np.int32)
-    mask_o, best_o = oracle.labels_from_costs(ev, hp, cand, 6)
+    lab_o, best_o = oracle.labels_listed(ev, hp, cand)
     t = lambda a: torch.from_numpy(a).to(DEV)
-    mask = torch.zeros((2, 6), dtype=torch.int8, device=DEV)
+    lab = torch.zeros((2, 5), dtype=torch.int8, device=DEV)
     best = torch.zeros(2, dtype=torch.int32, device=DEV)
-    ann.ann_hub_labels(t(ev), t(hp), t(cand), 2, 5, 6, 3, 15, mask, best)
+    ann.ann_hub_labels(t(ev), t(hp), t(cand), 2, 5, 3, 15, lab, best)
     torch.cuda.synchronize()
-    assert np.array_equal(mask.cpu().numpy(), mask_o)
+    assert np.array_equal(lab.cpu().numpy(), lab_o)
+    assert lab_o.tolist() == [[1, 1, 1, -1, 0], [-1, -1, -1, -1, -1]]
     assert best.cpu().numpy().tolist() == best_o.tolist() == [1, -1]
 
 

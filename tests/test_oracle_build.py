@@ -181,6 +181,40 @@ def test_labels_rule_hand_case():
     assert mask[0, 3] == 0  # hops 12: neither (7 < 12 < 19)
 
 
+def test_listed_labels_hand_case():
+    # the hand case above, labels per listed hub: cand [4, 0, 1, 2, 3] with
+    # hops [6, 5, 4, unreached, 25] -> +1 +1 +1 -1 -1 (hub 5 is not listed: a
+    # negative wherever the labels are used)
+    I = oracle.INT32_MAX
+    cand = np.array([[4, 0, 1, 2, 3], [0, 1, 2, 3, 4]])
+    evals = np.array([[50, 40, 40, I, 300], [I, I, I, I, I]])
+    hops = np.array([[6, 5, 4, I, 25], [I, I, I, I, I]])
+    lab, best = oracle.labels_listed(evals, hops, cand)
+    assert lab.tolist() == [[1, 1, 1, -1, -1], [-1, -1, -1, -1, -1]]
+    assert best.tolist() == [1, -1]
+    lab, _ = oracle.labels_listed(evals[:1], np.array([[6, 5, 4, I, 12]]), cand[:1])
+    assert lab[0].tolist() == [1, 1, 1, -1, 0]
+
+
+def test_listed_labels_expand_to_the_dense_rule():
+    # listing each query's searched hubs with their labels, every other hub a
+    # negative, is the dense label matrix of labels_from_costs
+    rng = np.random.default_rng(4)
+    nq, M, H = 60, 7, 20
+    cand = np.stack([rng.choice(H, M, replace=False) for _ in range(nq)])
+    hops = rng.integers(0, 30, (nq, M))
+    hops[rng.random((nq, M)) < 0.2] = oracle.INT32_MAX
+    hops[5] = oracle.INT32_MAX  # a query that reached nothing
+    evals = np.where(hops < oracle.INT32_MAX, hops * 10 + rng.integers(0, 10, (nq, M)), oracle.INT32_MAX)
+    for tp, tn in ((3, 15), (1, 5), (0, 1)):
+        lab, best = oracle.labels_listed(evals, hops, cand, tp, tn)
+        dense = np.full((nq, H), -1, np.int8)
+        np.put_along_axis(dense, cand, lab, axis=1)
+        ref, ref_best = oracle.labels_from_costs(evals, hops, cand, H, tp, tn)
+        assert np.array_equal(dense, ref)
+        assert np.array_equal(best, ref_best)
+
+
 def test_hub_costs_match_individual_searches():
     rng = np.random.default_rng(1)
     base = rng.integers(0, 256, (400, 16)).astype(np.uint8)

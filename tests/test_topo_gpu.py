@@ -17,6 +17,7 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("needs a CUDA device", allow_module_level=True)
 DEV = torch.device("cuda:0")
+from gpu_util import dense_as_listed  # noqa: E402
 
 
 def _tokens(h_idx, hubs, hops, max_nodes=4096):
@@ -96,7 +97,7 @@ def test_fusion_step_matches_oracle():
         dP, dU_ = torch.from_numpy(P).to(DEV), torch.from_numpy(U).to(DEV)
         ann.ann_trainer_set_fusion(t, dP, dU_, T, dU, heads, dk, WQ, WK, WV, WO)
         rows = torch.arange(B, dtype=torch.int32, device=DEV)
-        loss = ann.ann_trainer_step(t, torch.from_numpy(X).to(DEV), rows, B, torch.from_numpy(mask).to(DEV),
+        loss = ann.ann_trainer_step(t, torch.from_numpy(X).to(DEV), rows, B, *dense_as_listed(mask),
                                     apply_update=False)
         Eeff = np.zeros((H, 64), np.float32)
         gE = np.zeros((H, 64), np.float32)
@@ -139,7 +140,7 @@ def test_fusion_training_lowers_the_loss():
             ann.ann_trainer_set_fusion(t, torch.zeros((H, D), device=DEV), torch.zeros((H, T, dU), device=DEV),
                                        T, dU, 2, 16, WQ, WK, WV, WO)
         losses = torch.zeros(4 * 10, device=DEV)
-        ann.ann_trainer_fit(t, torch.from_numpy(X).to(DEV), 4096, torch.from_numpy(mask).to(DEV), None, 10, losses)
+        ann.ann_trainer_fit(t, torch.from_numpy(X).to(DEV), 4096, *dense_as_listed(mask), None, 10, losses)
         ls = losses.cpu().numpy()
         w0 = np.zeros_like(WO)
         ann.ann_trainer_get_fusion(t, None, None, None, w0)

@@ -17,6 +17,7 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("needs a CUDA device", allow_module_level=True)
 DEV = torch.device("cuda:0")
+from gpu_util import dense_as_listed  # noqa: E402
 
 
 def _problem(B=700, D=128, H=200, seed=0):
@@ -50,9 +51,8 @@ def test_gradients_match_oracle(B):
     t = ann.ann_trainer_create(128, W1, b1, W2, b2, E, 4096, tau=tau, lr=1e-3)
     try:
         dX = torch.from_numpy(X).to(DEV)
-        dm = torch.from_numpy(mask).to(DEV)
         dr = torch.from_numpy(rows).to(DEV)
-        loss = ann.ann_trainer_step(t, dX, dr, len(rows), dm, apply_update=False)
+        loss = ann.ann_trainer_step(t, dX, dr, len(rows), *dense_as_listed(mask), apply_update=False)
         g = {k: np.zeros_like(v) for k, v in dict(W1=W1, b1=b1, W2=W2, b2=b2, E=E).items()}
         ann.ann_trainer_get(t, g["W1"], g["b1"], g["W2"], g["b2"], g["E"], gradients=True)
     finally:
@@ -92,11 +92,10 @@ def test_training_lowers_the_loss_and_attaches():
     t = ann.ann_trainer_create(128, W1, b1, W2, b2, E, 512, tau=0.1, lr=3e-3)
     try:
         dX = torch.from_numpy(X).to(DEV)
-        dm = torch.from_numpy(mask).to(DEV)
         nt = len(X)
         steps = (nt + 511) // 512
         losses = torch.zeros(30 * steps, device=DEV)
-        ann.ann_trainer_fit(t, dX, nt, dm, None, 30, losses)
+        ann.ann_trainer_fit(t, dX, nt, *dense_as_listed(mask), None, 30, losses)
         ls = losses.cpu().numpy()
         assert ls[-steps:].mean() < 0.5 * ls[:steps].mean()
         W = np.zeros_like(W1)
@@ -104,3 +103,33 @@ def test_training_lowers_the_loss_and_attaches():
         assert np.isfinite(W).all() and not np.array_equal(W, W1)
     finally:
         ann.ann_trainer_free(t)
+
+
+def test_listed_labels_train_like_their_dense_matrix():
+    # M listed hubs per query (the label search's candidates), every other hub
+    # a negative: the same loss and gradients as the dense label matrix that
+    # lists all hubs (only the label layout differs)
+    X, W1, b1, W2, b2, E, _, rows = _problem(B=900, H=300, seed=4)
+    rng = np.random.default_rng(8)
+    n, H, M = len(X), 300, 40
+    cand = np.stack([rng.choice(H, M, replace=False) for _ in range(n)]).astype(np.int32)
+    lab = rng.choice(np.array([-1, 0, 1], np.int8), size=(n, M), p=[0.3, 0.4, 0.3])
+    cand[7, 5] = -1  # an empty slot
+    dense = np.full((n, H), -1, np.int8)
+    for r in range(n):
+        ok = cand[r] >= 0
+        dense[r, cand[r][ok]] = lab[r][ok]
+    out = []
+    for labels in ((torch.from_numpy(cand).to(DEV), torch.from_numpy(lab).to(DEV), M), dense_as_listed(dense)):
+        t = ann.ann_trainer_create(128, W1, b1, W2, b2, E, 1024, tau=0.1, lr=1e-3)
+        try:
+            loss = ann.ann_trainer_step(t, torch.from_numpy(X).to(DEV), torch.from_numpy(rows).to(DEV), len(rows),
+                                        *labels, apply_update=False)
+            gE = np.zeros_like(E)
+            ann.ann_trainer_get(t, hub_emb=gE, gradients=True)
+        finally:
+            ann.ann_trainer_free(t)
+        out.append((loss, gE))
+    assert out[0][0] == out[1][0]
+    # the reductions over the batch may add partial sums in another order
+    assert _rel(out[0][1], out[1][1]) <= 1e-5
