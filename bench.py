@@ -187,6 +187,14 @@ def parse():
                     help="streams that consecutive batches alternate over in the timed steps")
     ap.add_argument("--fixed-L", type=int, default=0,
                     help="skip the L sweep and run every entry mode at this pool size")
+    ap.add_argument("--alpha", type=float, default=1.0,
+                    help="RNG pruning factor of the graph builder (c is dropped when a kept s has "
+                         "alpha * d(s, c) <= d(p, c); above 1 keeps more long edges)")
+    ap.add_argument("--spectrum", type=float, default=None,
+                    help="exponent of the per-dimension variance spectrum (1+i)^-2e of the synthetic "
+                         "law (0: isotropic); default: the workload's")
+    ap.add_argument("--centre-scale", type=float, default=None,
+                    help="spread of the mixture centres (shift and batch laws); default: the workload's")
     args = ap.parse_args()
     spec = dict(WORKLOADS[args.workload])
     if args.n:
@@ -205,6 +213,18 @@ def parse():
         spec["n_train"] = 0
     if args.fixed_L:
         spec["fixed_L"] = args.fixed_L
+    spec["alpha"] = args.alpha
+    law = {}
+    if args.spectrum is not None:
+        law["spectrum"] = args.spectrum
+    if args.centre_scale is not None:
+        if spec["gen"] not in ("shift_f32", "batch_f32", "highdim_f32"):
+            raise SystemExit("--centre-scale applies to the shift, batch and highdim laws")
+        law["centre_scale"] = args.centre_scale
+    spec["law"] = law
+    if law or args.alpha != 1.0:
+        spec["desc"] += "; " + ", ".join([f"{k}={v}" for k, v in law.items()] +
+                                         [f"graph alpha={args.alpha}"])
     # W * R may not exceed 128 candidates per step
     args.W = max(1, min(args.W, 128 // spec["R"]))
     args.spec = spec
@@ -308,14 +328,15 @@ def recall(ids, gt, k=K_NN):
 
 def generate(spec, synth):
     g = spec["gen"]
+    law = spec.get("law", {})
     if g == "shift_f32":
-        return synth.shift_f32(n=spec["n"], nq=spec["nq"], n_train=spec["n_train"])
+        return synth.shift_f32(n=spec["n"], nq=spec["nq"], n_train=spec["n_train"], **law)
     if g == "ip_f32":
-        return synth.ip_f32(n=spec["n"], nq=spec["nq"], n_train=spec["n_train"])
+        return synth.ip_f32(n=spec["n"], nq=spec["nq"], n_train=spec["n_train"], **law)
     if g == "highdim_f32":
-        return synth.highdim_f32(n=spec["n"], nq=spec["nq"])
+        return synth.highdim_f32(n=spec["n"], nq=spec["nq"], **law)
     if g == "batch_f32":
-        return synth.batch_f32(n=spec["n"], nq=spec["nq"], n_train=spec["n_train"])
+        return synth.batch_f32(n=spec["n"], nq=spec["nq"], n_train=spec["n_train"], **law)
     return synth.small_u8(n=spec["n"], nq=spec["nq"])
 
 
@@ -334,10 +355,10 @@ def build_workload(args, torch, ann, synth, dev):
     # neighbours exactly as the inner product does
     if spec.get("insert"):
         # tens of millions of rows: insertion by search after an exact seed graph
-        med, rep = ann.ann_build_graph_insert(base, n, dim, dt, 64, R, 1.0, spec["insert"][0], spec["insert"][1],
-                                              graph)
+        med, rep = ann.ann_build_graph_insert(base, n, dim, dt, 64, R, spec.get("alpha", 1.0), spec["insert"][0],
+                                              spec["insert"][1], graph)
     else:
-        med, rep = ann.ann_build_graph(base, n, dim, dt, 64, R, 1.0, graph)
+        med, rep = ann.ann_build_graph(base, n, dim, dt, 64, R, spec.get("alpha", 1.0), graph)
     t_build = time.time() - t0
     q = torch.from_numpy(w["queries"]).to(dev)
     nq = q.shape[0]

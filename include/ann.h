@@ -653,6 +653,38 @@ ann_status ann_hub_costs(ann_index *idx, const void *d_queries, int64_t nq, cons
 ann_status ann_hub_labels(const int32_t *d_evals, const int32_t *d_hops, const int32_t *d_cand, int64_t nq,
                           int32_t M, int32_t t_pos, int32_t t_neg, int8_t *d_labels, int32_t *d_best, void *stream);
 
+/* ---- base-partitioned search: the exchange step -------------------------- */
+/*
+ * The base set split into P shards (groups of whole hub clusters, Sec. 4.1,
+ * Def. 3), each with its own index searched by ann_search_batch; a query's
+ * answer is the k best of the shards' answers under the (distance, id) order
+ * of Sec. 2.1, Problem 1.  These two calls are the steps around the exchange
+ * of the shards' answers.
+ */
+
+/*
+ * Shard-local row ids to global ids, in place: d_ids[i] >= 0 becomes
+ * d_map[d_ids[i]]; -1 stays -1.  An id >= n_map becomes -1 and sets bit 0 of
+ * *d_status (device int32, optional, OR-ed).  Asynchronous;
+ * ANN_ERR_INVALID_ARG for a NULL array with count > 0.
+ */
+ann_status ann_map_ids(int32_t *d_ids, int64_t count, const int32_t *d_map, int64_t n_map, int32_t *d_status,
+                       void *stream);
+
+/*
+ * Merge of P answer lists per query: d_ids / d_dists hold P blocks of nq x k
+ * (block p = shard p's answers, row-major [P][nq][k]), each row sorted by
+ * (distance, id) with (-1, +inf) padding, ids global and distinct across
+ * the lists (the shards are disjoint).  Writes the k smallest (distance, id)
+ * of each query's P*k entries to d_out_ids / d_out_dists (nq x k), padded
+ * with (-1, +inf) (INT32_MAX for int distances).
+ *   int_dists  non-zero: distances are int32 (uint8 data), else fp32
+ *   P          1..32
+ * Asynchronous; ANN_ERR_INVALID_ARG for P or k out of range or NULL buffers.
+ */
+ann_status ann_merge_shards(const int32_t *d_ids, const void *d_dists, int32_t P, int64_t nq, int32_t k,
+                            int32_t int_dists, int32_t *d_out_ids, void *d_out_dists, void *stream);
+
 /* ---- offline construction (GPU) ------------------------------------------ */
 
 /*

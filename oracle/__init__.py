@@ -360,6 +360,23 @@ def labels_listed(evals, hops, cand, t_pos=3, t_neg=15):
     return lab, best
 
 
+def merge_answers(ids_list, dists_list, k):
+    """Answer of a base-partitioned search: per query, the k smallest
+    (distance, id) pairs of the union of the shards' answers (Sec. 2.1,
+    Problem 1's order; -1 entries are empty), padded with (-1, +inf).
+    ids_list / dists_list: one [nq, k_s] array per shard, ids global.
+    Returns (ids int32 [nq, k], dists float64 [nq, k])."""
+    nq = len(ids_list[0])
+    ids = np.full((nq, k), -1, np.int32)
+    dists = np.full((nq, k), np.inf)
+    for i in range(nq):
+        pairs = sorted((float(d[i, j]), int(a[i, j])) for a, d in zip(ids_list, dists_list)
+                       for j in range(a.shape[1]) if a[i, j] >= 0)[:k]
+        for j, (dv, iv) in enumerate(pairs):
+            ids[i, j], dists[i, j] = iv, dv
+    return ids, dists
+
+
 def pruned_row(base, p, K, R, alpha=1.0):
     """Steps 1-2 of the graph builder (Sec. 2.1, Def. 1) for the single node p:
     its K exact nearest other nodes by (dist, id), then relative-neighbourhood

@@ -108,6 +108,8 @@ def load_library(path: str | None = None):
         "ann_trainer_get_fusion": ([_p, _p, _p, _p, _p, i32], i32),
         "ann_hub_costs": ([_p, _p, i64, _p, _p, i32, _p, i32, i32, _p, _p, _p], i32),
         "ann_hub_labels": ([_p, _p, _p, i64, i32, i32, i32, _p, _p, _p], i32),
+        "ann_map_ids": ([_p, i64, _p, i64, _p, _p], i32),
+        "ann_merge_shards": ([_p, _p, i32, i64, i32, i32, _p, _p, _p], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -377,6 +379,18 @@ def ann_hub_labels(evals, hops, cand, nq, M, t_pos, t_neg, labels, best=None, st
     _check(load_library().ann_hub_labels(_ptr(evals), _ptr(hops), _ptr(cand), int(nq), int(M),
                                          int(t_pos), int(t_neg), _ptr(labels), _ptr(best), _stream(stream)),
            "ann_hub_labels")
+
+
+def ann_map_ids(ids, count, id_map, n_map, status=None, stream=None):
+    """Shard-local ids to global ids in place (device int32 arrays)."""
+    _check(load_library().ann_map_ids(_ptr(ids), int(count), _ptr(id_map), int(n_map), _ptr(status),
+                                      _stream(stream)), "ann_map_ids")
+
+
+def ann_merge_shards(ids, dists, P, nq, k, int_dists, out_ids, out_dists, stream=None):
+    """k best (distance, id) of P sorted answer lists per query (device)."""
+    _check(load_library().ann_merge_shards(_ptr(ids), _ptr(dists), int(P), int(nq), int(k), int(bool(int_dists)),
+                                           _ptr(out_ids), _ptr(out_dists), _stream(stream)), "ann_merge_shards")
 
 
 def ann_select_entry_noalloc(h, queries, nq, entry_out, qhat_out=None, stream=None):

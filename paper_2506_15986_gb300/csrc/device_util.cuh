@@ -113,9 +113,12 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
 // bits 31..1 = node id, bit 0 = "expanded" flag.  Comparing keys with bit 0
 // cleared is the (distance, id) order; ids are < 2^31.
 
+// Order-preserving bits of a float distance.  -0 is folded into +0 first
+// (x + 0 rounds -0 to +0 and leaves every other value unchanged), so the two
+// zeros are one distance and ties between them go to the smaller id.
 __device__ __forceinline__ uint32_t f32_to_ord(float f)
 {
-    uint32_t u = __float_as_uint(f);
+    const uint32_t u = __float_as_uint(__fadd_rn(f, 0.0f));
     return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
 

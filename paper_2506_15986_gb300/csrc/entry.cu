@@ -363,6 +363,107 @@ __global__ void map_hub_seeds(const int32_t *hub_ids, int64_t nq, int m, const i
     }
 }
 
+// ---- hub-graph search (Sec. 4.3: Algorithm 1 on the high-tier hub graph) ----
+// One warp per query, pools of at most 32 hubs: lane i holds the i-th
+// smallest (score, hub) key of the pool (bit 0: expanded), so a step is a
+// ballot for the first unexpanded entry, one adjacency row read by lanes
+// 0..s-1, a visited test-and-set in a per-warp shared-memory bitmap over the
+// hubs, the fresh neighbours scored lane-parallel (-q_hat . e_hat in FP32
+// over the BF16 hub rows), a 32-key bitonic sort of the new keys and a
+// bitonic merge with the pool, truncated to L.  The steps and the pool
+// follow the sorted-pool reading of Algorithm 1 with W = 1: the pool is the
+// L smallest keys of every hub evaluated, a hub is evaluated once, the search
+// stops when no unexpanded entry is left.  The m best pool entries become the
+// seeds (their hubs' nodes).
+constexpr int kNavWarps = 8;
+constexpr int kNavMaxPool = 32;
+
+__device__ __forceinline__ float hub_score(const float *q, const __nv_bfloat16 *row)
+{
+    // -<q, e> with four FP32 accumulators over coordinates j mod 4
+    const uint4 *r4 = reinterpret_cast<const uint4 *>(row);
+    const float4 *q4 = reinterpret_cast<const float4 *>(q);
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll 4
+    for (int c = 0; c < 8; ++c) {
+        const uint4 x = __ldg(r4 + c);
+        const float4 qa = q4[2 * c], qb = q4[2 * c + 1];
+        const float2 f0 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&x.x));
+        const float2 f1 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&x.y));
+        const float2 f2 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&x.z));
+        const float2 f3 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&x.w));
+        a0 = fmaf(f0.x, qa.x, a0);
+        a1 = fmaf(f0.y, qa.y, a1);
+        a2 = fmaf(f1.x, qa.z, a2);
+        a3 = fmaf(f1.y, qa.w, a3);
+        a0 = fmaf(f2.x, qb.x, a0);
+        a1 = fmaf(f2.y, qb.y, a1);
+        a2 = fmaf(f3.x, qb.z, a2);
+        a3 = fmaf(f3.y, qb.w, a3);
+    }
+    return -((a0 + a1) + (a2 + a3));
+}
+
+__global__ void __launch_bounds__(32 * kNavWarps, 4)
+    hub_nav_kernel(const float *qhat, int64_t nq, const __nv_bfloat16 *Eb, int H, const int32_t *hgraph, int s,
+                   int32_t entry, int L, int m_seeds, const int32_t *hub_nodes, int32_t medoid, int bm_words,
+                   int32_t *out)
+{
+    extern __shared__ __align__(16) uint8_t nav_smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int per_warp = 256 + 4 * bm_words;
+    float *q = reinterpret_cast<float *>(nav_smem + wid * per_warp);
+    uint32_t *vis = reinterpret_cast<uint32_t *>(nav_smem + wid * per_warp + 256);
+    for (int64_t qi = blockIdx.x * static_cast<int64_t>(kNavWarps) + wid; qi < nq;
+         qi += static_cast<int64_t>(gridDim.x) * kNavWarps) {
+        if (lane < 16)
+            reinterpret_cast<float4 *>(q)[lane] = reinterpret_cast<const float4 *>(qhat + qi * 64)[lane];
+        for (int w = lane; w < bm_words; w += 32)
+            vis[w] = 0u;
+        __syncwarp();
+        // the initial pool: the entry hub, evaluated
+        uint64_t pool = kKeyMax;
+        if (lane == 0) {
+            vis[entry >> 5] = 1u << (entry & 31);
+            pool = make_key(f32_to_ord(hub_score(q, Eb + static_cast<int64_t>(entry) * 64)), entry);
+        }
+        for (;;) {
+            const unsigned um = __ballot_sync(kFull, lane < L && pool != kKeyMax && !(pool & 1ull));
+            if (!um)
+                break;
+            const int f = __ffs(um) - 1;
+            if (lane == f)
+                pool |= 1ull;
+            const int32_t node = __shfl_sync(kFull, key_id(pool), f);
+            __syncwarp();
+            const int32_t nb = lane < s ? __ldg(hgraph + static_cast<int64_t>(node) * s + lane) : -1;
+            uint64_t cand = kKeyMax;
+            if (nb >= 0 && nb < H) {
+                const uint32_t bit = 1u << (nb & 31);
+                if (!(atomicOr(&vis[nb >> 5], bit) & bit))
+                    cand = make_key(f32_to_ord(hub_score(q, Eb + static_cast<int64_t>(nb) * 64)), nb);
+            }
+            cand = warp_sort32(cand, lane);
+            // the 32 smallest of two ascending sequences: pairwise minima of
+            // one against the other reversed form a bitonic sequence, which
+            // five half-cleaner stages sort
+            const uint64_t rc = __shfl_sync(kFull, cand, 31 - lane);
+            uint64_t mn = pool < rc ? pool : rc;
+#pragma unroll
+            for (int j = 16; j > 0; j >>= 1) {
+                const uint64_t o = __shfl_xor_sync(kFull, mn, j);
+                mn = (lane & j) ? kmax(mn, o) : kmin(mn, o);
+            }
+            pool = lane < L ? mn : kKeyMax;
+        }
+        if (lane < m_seeds) {
+            const int32_t hub = pool != kKeyMax ? key_id(pool) : -1;
+            out[qi * m_seeds + lane] = hub >= 0 ? hub_nodes[hub] : (lane == 0 ? medoid : -1);
+        }
+        __syncwarp();
+    }
+}
+
 // medoid seed sets: the medoid first, the other slots unused
 __global__ void fill_medoid_seeds(int32_t *out, int64_t nq, int m, int32_t medoid)
 {
@@ -683,6 +784,22 @@ ann_status ann_select_entries(ann_index *idx, const void *d_queries, int64_t nq,
     if (st == ANN_OK && mode == ANN_ENTRY_LEARNED_EXHAUSTIVE) {
         const Operand Q{qbf, OP_BF16, 64, 1, nq, 64, nullptr};
         st = launch_hub_argmax(m, Q, nq, d_entry, hid, hsc, idx->d_status, s, m_seeds);
+    } else if (st == ANN_OK && L_hub <= kNavMaxPool && m->s <= 32) {
+        // the hub-graph search in one launch (pools of up to 32 hubs)
+        const int bm_words = (m->H + 127) / 128 * 4;
+        const size_t per_warp = 256 + 4 * static_cast<size_t>(bm_words);
+        const size_t smem = per_warp * kNavWarps;
+        cudaError_t e = cudaFuncSetAttribute(hub_nav_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(smem));
+        if (e == cudaSuccess) {
+            const int64_t blocks = std::min<int64_t>((nq + kNavWarps - 1) / kNavWarps,
+                                                     static_cast<int64_t>(idx->num_sms) * 8);
+            hub_nav_kernel<<<static_cast<unsigned>(blocks), 32 * kNavWarps, smem, s>>>(
+                qhat, nq, m->Eb, m->H, m->hub_graph, m->s, m->hub_entry, L_hub, m_seeds, m->hub_nodes, idx->medoid,
+                bm_words, d_entry);
+            e = cudaGetLastError();
+        }
+        st = cuda_status(e);
     } else if (st == ANN_OK) {
         ann_search_params p{};
         p.k = m_seeds;

@@ -3,8 +3,10 @@ of the guided subgraph walk (Sec. 4.2) bit for bit against the oracle (both
 sides rank and sum in float32 in the same order), and the fusion embedding
 (Sec. 4.3, Eq. fusion) inside a training step against the float64 oracle at
 the trainer's tolerances (BF16 GEMM operands, FP32 accumulation: gradients by
-relative Frobenius error <= 3e-2 and cosine >= 0.999, the loss within 2e-3;
-the fusion itself runs in FP32: its output within 1e-4)."""
+relative Frobenius error <= 8e-3 and cosine >= 0.99995, the loss within 1e-4,
+twice the largest errors measured on a GB300 (2.8e-3 relative Frobenius for
+E, WQ and WK, 5e-4 for WV and WO, cosine >= 0.999996, loss 1.1e-5); the
+fusion itself runs in FP32: its output within 1e-5 (measured 6e-7))."""
 import numpy as np
 import pytest
 
@@ -110,18 +112,18 @@ def test_fusion_step_matches_oracle():
     F, cache = ot.fusion_forward(P.astype(np.float64), U.astype(np.float64), WQ.astype(np.float64),
                                  WK.astype(np.float64), WV.astype(np.float64), WO.astype(np.float64), heads)
     Ee = E.astype(np.float64) + F
-    np.testing.assert_allclose(Eeff, Ee, rtol=1e-4, atol=1e-4)
+    np.testing.assert_allclose(Eeff, Ee, rtol=1e-5, atol=1e-5)
     bf = ot.bf16_round
     ref_loss, ref = ot.loss_and_grads(bf(X), bf(W1), b1.astype(np.float64), bf(W2), b2.astype(np.float64), Ee,
                                       mask, tau)
-    assert abs(loss - ref_loss) <= 2e-3 * abs(ref_loss)
+    assert abs(loss - ref_loss) <= 1e-4 * abs(ref_loss)
     rel = lambda a, b: np.linalg.norm(a - b) / np.linalg.norm(b)
     cos = lambda a, b: float((a * b).sum() / (np.linalg.norm(a) * np.linalg.norm(b)))
-    assert rel(gE, ref["E"]) <= 3e-2 and cos(gE, ref["E"]) >= 0.999
+    assert rel(gE, ref["E"]) <= 8e-3 and cos(gE, ref["E"]) >= 0.99995
     refw = ot.fusion_backward(ref["E"], cache, WO.astype(np.float64))
     for name, g, r in zip(("WQ", "WK", "WV", "WO"), gw, refw):
-        assert rel(g, r) <= 3e-2, (name, rel(g, r))
-        assert cos(g, r) >= 0.999, (name, cos(g, r))
+        assert rel(g, r) <= 8e-3, (name, rel(g, r))
+        assert cos(g, r) >= 0.99995, (name, cos(g, r))
 
 
 def test_fusion_training_lowers_the_loss():

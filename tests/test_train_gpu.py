@@ -2,10 +2,14 @@
 
 Tolerance: every GEMM of a step takes BF16 operands (about 2^-9 relative
 rounding each) with FP32 accumulation, and the backward pass chains up to
-four such GEMMs, so each parameter's gradient is compared by its relative
-Frobenius error (<= 3e-2) and cosine (>= 0.999) against the oracle fed the
-same BF16-rounded inputs; the loss within 2e-3 relative.  Adam is elementwise
-fp32 against float64: 1e-5 relative."""
+four such GEMMs whose intermediate operands (the logit gradients, dq_hat, the
+hidden layer's gradient) are rounded again, which the oracle fed the same
+BF16-rounded inputs does not do.  Measured on a GB300 over batches of 700,
+3,000 and 8,192 rows (three seeds each): relative Frobenius error 2.0e-3 to
+4.0e-3 per parameter, cosine >= 0.99999, loss within 2.5e-5 relative.  The
+bars are twice the largest measured error: relative Frobenius <= 8e-3,
+cosine >= 0.99995, loss within 1e-4 relative.  Adam is elementwise fp32
+against float64: 1e-5 relative."""
 import numpy as np
 import pytest
 
@@ -60,10 +64,10 @@ def test_gradients_match_oracle(B):
     bf = ot.bf16_round
     ref_loss, ref = ot.loss_and_grads(bf(X[rows]), bf(W1), b1.astype(np.float64), bf(W2),
                                       b2.astype(np.float64), E.astype(np.float64), mask[rows], tau)
-    assert abs(loss - ref_loss) <= 2e-3 * abs(ref_loss)
+    assert abs(loss - ref_loss) <= 1e-4 * abs(ref_loss)
     for k in ("W1", "b1", "W2", "b2", "E"):
-        assert _rel(g[k], ref[k]) <= 3e-2, (k, _rel(g[k], ref[k]))
-        assert _cos(g[k], ref[k]) >= 0.999, (k, _cos(g[k], ref[k]))
+        assert _rel(g[k], ref[k]) <= 8e-3, (k, _rel(g[k], ref[k]))
+        assert _cos(g[k], ref[k]) >= 0.99995, (k, _cos(g[k], ref[k]))
 
 
 def test_adam_update_matches_oracle():
