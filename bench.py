@@ -187,6 +187,9 @@ def parse():
                     help="streams that consecutive batches alternate over in the timed steps")
     ap.add_argument("--fixed-L", type=int, default=0,
                     help="skip the L sweep and run every entry mode at this pool size")
+    ap.add_argument("--knobs", default="",
+                    help="fixed search sizes hash_bits,stage_rows,team,spill_bits,gather instead of ann_autotune "
+                         "(for a profiler capture of one known configuration)")
     ap.add_argument("--alpha", type=float, default=1.0,
                     help="RNG pruning factor of the graph builder (c is dropped when a kept s has "
                          "alpha * d(s, c) <= d(p, c); above 1 keeps more long edges)")
@@ -563,7 +566,7 @@ class Runner:
                                          self.dists, 10, self.stream, lanes=max(1, self.args.lanes))
         self.tuned[L] = best
         return {"hash_bits": best.hash_bits, "stage_rows": best.stage_rows, "team": best.team,
-                "spill_bits": best.spill_bits,
+                "spill_bits": best.spill_bits, "gather": best.gather,
                 "search_ms": ms}
 
     def select(self, q):
@@ -776,7 +779,14 @@ def measure_mode(run, torch, ann, W, args, targets):
         Lstar, sw, per = args.spec["fixed_L"], [], {}
     else:
         Lstar, sw, per = sweep(run, torch, ann, W, targets)
-    tune = None if args.no_tune else run.autotune(Lstar)
+    if args.knobs:
+        hb, sr, tm, sb, ga = (int(x) for x in args.knobs.split(","))
+        p = run.params(Lstar)
+        p.hash_bits, p.stage_rows, p.team, p.spill_bits, p.gather = hb, sr, tm, sb, ga
+        run.tuned[Lstar] = p
+        tune = {"hash_bits": hb, "stage_rows": sr, "team": tm, "spill_bits": sb, "gather": ga, "fixed": True}
+    else:
+        tune = None if args.no_tune else run.autotune(Lstar)
     run.step(Lstar, stats=True)
     torch.cuda.synchronize()
     s = run.stats.cpu().numpy().astype(np.int64)
@@ -907,7 +917,7 @@ def batch_report(W, torch, ann, args, dev, modes):
         for b0 in range(0, nq, B):
             sl = slice(b0, b0 + B)
             pb = ann.search_params(100, 512, W=args.W, hash_bits=best.hash_bits, stage_rows=best.stage_rows,
-                                   team=best.team, spill_bits=best.spill_bits, d_k=kq[sl], d_L=Lq[sl],
+                                   team=best.team, spill_bits=best.spill_bits, gather=best.gather, d_k=kq[sl], d_L=Lq[sl],
                                    n_entries=ns)
             a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
@@ -919,7 +929,7 @@ def batch_report(W, torch, ann, args, dev, modes):
         ib = torch.empty((B, 100), dtype=torch.int32, device=dev)
         db = torch.empty((B, 100), dtype=torch.float32, device=dev)
         pp = ann.search_params(100, 512, W=args.W, hash_bits=best.hash_bits, stage_rows=best.stage_rows,
-                               team=best.team, spill_bits=best.spill_bits, d_k=kb, d_L=lb, n_entries=ns)
+                               team=best.team, spill_bits=best.spill_bits, gather=best.gather, d_k=kb, d_L=lb, n_entries=ns)
         plan = ann.ann_plan_create(W["h"], qb, B, em, args.l_hub, pp, None if em == ann.ENTRY_MEDOID else eb,
                                    ib, db)
         try:
@@ -936,7 +946,7 @@ def batch_report(W, torch, ann, args, dev, modes):
             "qps_one_launch": qps, "recall_at_own_k": rec, "queries": nq,
             "evals_per_query": float(s[:, 0].mean()), "hops_per_query": float(s[:, 1].mean()),
             "tuned": {"hash_bits": best.hash_bits, "stage_rows": best.stage_rows, "team": best.team,
-                      "spill_bits": best.spill_bits},
+                      "spill_bits": best.spill_bits, "gather": best.gather},
             "batch": B, "batch_latency_ms": {"p50": float(np.percentile(lat, 50)),
                                              "p99": float(np.percentile(lat, 99))},
             "plan_latency_ms": {"p50": float(np.percentile(lat_plan, 50)),
@@ -1014,7 +1024,7 @@ def run_gpu(args):
     for mt in MEASURED_TRAFFIC.get(args.workload, []):
         if mt["digest"] == kernel_digest() and mt["entry"] == head and mt["L"] == R["L"] \
                 and mt["nq"] == R["run"].nq \
-                and all(tn.get(key) == mt[key] for key in ("hash_bits", "stage_rows", "team", "spill_bits")):
+                and all(tn.get(key) == mt[key] for key in ("hash_bits", "stage_rows", "team", "spill_bits", "gather")):
             traffic = mt["bytes"]
     out = None
     if rank == 0:

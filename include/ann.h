@@ -137,6 +137,10 @@ typedef struct {
  *             limit had passed: each query fails with -1 ids and the call
  *             reports ANN_ERR_TIMEOUT through ann_sync_status.  The copies in
  *             flight still land, so the device and the index stay usable.
+ *   gather    how a round of neighbour rows is fetched, 0 = chosen from the
+ *             row size; 1: one bulk copy per row; 4: one TMA tensor gather per
+ *             four rows (rows of 32-byte multiples up to 1 KiB; other sizes
+ *             use 1).  Speed only, never results (see ann_autotune)
  *   d_k, d_L  optional per-query k and L (device int32[nq]); NULL = k, L
  *   d_target  optional per-query target node (device int32[nq]); when given
  *             the search runs in label mode: it stops after the step in which
@@ -153,6 +157,7 @@ typedef struct {
     int32_t spill_bits;
     int32_t n_entries;
     uint32_t flags;
+    int32_t gather;
     const int32_t *d_k;
     const int32_t *d_L;
     const int32_t *d_target;

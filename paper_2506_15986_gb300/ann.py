@@ -36,7 +36,7 @@ class ann_search_params(ctypes.Structure):
     _fields_ = [("k", _c.c_int32), ("L", _c.c_int32), ("W", _c.c_int32),
                 ("hash_bits", _c.c_int32), ("stage_rows", _c.c_int32), ("team", _c.c_int32),
                 ("spill_bits", _c.c_int32), ("n_entries", _c.c_int32),
-                ("flags", _c.c_uint32), ("d_k", _p),
+                ("flags", _c.c_uint32), ("gather", _c.c_int32), ("d_k", _p),
                 ("d_L", _p), ("d_target", _p)]
 
 
@@ -202,10 +202,10 @@ def ann_load_index(path, device=0):
 
 
 def search_params(k, L, W=1, hash_bits=0, flags=0, d_k=None, d_L=None, d_target=None,
-                  stage_rows=0, team=0, spill_bits=0, n_entries=0):
+                  stage_rows=0, team=0, spill_bits=0, n_entries=0, gather=0):
     return ann_search_params(k=int(k), L=int(L), W=int(W), hash_bits=int(hash_bits),
                              stage_rows=int(stage_rows), team=int(team), spill_bits=int(spill_bits),
-                             n_entries=int(n_entries),
+                             n_entries=int(n_entries), gather=int(gather),
                              flags=int(flags), d_k=_ptr(d_k), d_L=_ptr(d_L),
                              d_target=_ptr(d_target))
 

@@ -129,6 +129,44 @@ struct FileHeader {
 }  // namespace
 }  // namespace ann
 
+namespace ann {
+namespace {
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// Tensor map over the base rows for four-row TMA gathers: a 2-D tensor of
+// rowbytes / 4 four-byte elements by n rows, one-row boxes spanning a whole
+// row (at most 256 elements, so rows up to 1 KiB; a multiple of 32 bytes so
+// that four rows fill whole 128-byte lines of the staging area).  Leaves
+// has_row_map at 0 when the row size does not qualify or the driver lacks
+// the encoder, and the search then copies row by row.
+void make_row_map(ann_index *idx)
+{
+    idx->has_row_map = 0;
+    if (idx->rowbytes % 32 != 0 || idx->rowbytes > 1024)
+        return;
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+        return;
+    const cuuint64_t dims[2] = {static_cast<cuuint64_t>(idx->rowbytes / 4), static_cast<cuuint64_t>(idx->n)};
+    const cuuint64_t strides[1] = {static_cast<cuuint64_t>(idx->rowbytes)};
+    const cuuint32_t box[2] = {static_cast<cuuint32_t>(idx->rowbytes / 4), 1};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = reinterpret_cast<EncodeTiledFn>(fn)(
+        &idx->row_map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, idx->d_base, dims, strides, box, estr,
+        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    idx->has_row_map = r == CUDA_SUCCESS ? 1 : 0;
+}
+
+}  // namespace
+}  // namespace ann
+
 using namespace ann;
 
 extern "C" {
@@ -148,6 +186,7 @@ const char *ann_status_string(ann_status s)
     default: return "unknown status";
     }
 }
+
 
 ann_status ann_index_create(const ann_index_desc *desc, int device, ann_index **out)
 {
@@ -231,6 +270,7 @@ ann_status ann_index_create(const ann_index_desc *desc, int device, ann_index **
         destroy(idx);
         return st;
     }
+    make_row_map(idx);
     *out = idx;
     return ANN_OK;
 }
@@ -388,7 +428,8 @@ ann_status ann_search_batch(ann_index *idx, const void *d_queries, int64_t nq, c
         (p->hash_bits != 0 && p->hash_bits != -1 && (p->hash_bits < 8 || p->hash_bits > 15)) ||
         p->stage_rows < 0 ||
         p->stage_rows > 32 || p->team < 0 || p->team > 32 || (p->team & (p->team - 1)) != 0 ||
-        (p->spill_bits != 0 && (p->spill_bits < 10 || p->spill_bits > 16)) || p->n_entries < 0 ||
+        (p->spill_bits != 0 && (p->spill_bits < 10 || p->spill_bits > 16)) ||
+        (p->gather != 0 && p->gather != 1 && p->gather != 4) || p->n_entries < 0 ||
         p->n_entries > ANN_MAX_SEEDS || (p->n_entries > 1 && !d_entry))
         return ANN_ERR_INVALID_ARG;
     if (p->flags & ~(ANN_SEARCH_RERANK | ANN_SEARCH_FAULT_WAIT))

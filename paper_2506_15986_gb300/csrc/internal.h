@@ -1,6 +1,7 @@
 // internal.h -- host-side index object and kernel launchers of libann.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -25,6 +26,10 @@ struct ann_index {
     int *status_sink = nullptr;   // if set, kernels report here instead (hub index -> its parent)
     cudaMemPool_t pool = nullptr; // stream-ordered scratch
     ann_entry_model *model = nullptr;
+    // 2-D tensor map over the base rows (4-byte elements, one row per box)
+    // for TMA tensor gathers of four rows; valid when has_row_map
+    CUtensorMap row_map;
+    int has_row_map = 0;
 };
 
 namespace ann {

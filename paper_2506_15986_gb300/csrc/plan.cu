@@ -218,6 +218,25 @@ ann_status ann_autotune(ann_index *idx, const void *d_queries, int64_t nq, const
         c.spill_bits = sb;
         ok = trial(c);
     }
+    // stage 4: four-row TMA tensor gathers (when the index's rows allow
+    // them) at the best sizes so far, with larger rounds and eight-lane
+    // distance teams (the gathered rows are unpadded, so small teams read
+    // them with bank conflicts)
+    if (idx->has_row_map) {
+        const ann_search_params b3 = bp;
+        const int teams[2] = {b3.team > 0 ? b3.team : ann::default_team(idx->rowbytes), 8};
+        for (int sr : {8, 12, 16}) {
+            for (int ti = 0; ti < 2 && ok; ++ti) {
+                if (ti == 1 && teams[1] == teams[0])
+                    continue;
+                ann_search_params c = b3;
+                c.gather = 4;
+                c.stage_rows = sr;
+                c.team = teams[ti];
+                ok = trial(c);
+            }
+        }
+    }
     // the caller's outputs hold the chosen combination's results
     if (ok && bms < 1e30f)
         st = ann_search_batch(idx, d_queries, nq, d_entry, &bp, d_ids, d_dists, nullptr, s);

@@ -42,6 +42,8 @@ constexpr int kTimeoutIters = 1 << 22;
 constexpr int kSlots = ANN_MAX_STEP_CAND / 32;  // neighbour slots per lane in one step
 
 struct SearchArgs {
+    CUtensorMap row_map;  // four-row TMA gathers of base rows (gather4 only)
+    int gather4;          // 1: a round's rows come in TMA tensor gathers of four
     const uint8_t *base;
     const int32_t *graph;
     int64_t n;
@@ -70,7 +72,7 @@ struct SearchArgs {
     int off_sel, off_q, off_stage, off_pool, off_ptop, off_cbuf, off_hash, per_warp;
     int stage_rows, stage_stride;
     int team_lg;  // log2 of the lanes computing one distance
-    int cpl;      // 16-byte chunks of a row per lane when they divide evenly into 1, 2, 4 or 8, else 0
+    int cpl;      // 8 when a row is exactly 8 16-byte chunks per lane (unrolled), else 0
 };
 
 __device__ __forceinline__ uint32_t hash_slot(uint32_t key, int bits)
@@ -334,19 +336,26 @@ __device__ __forceinline__ uint32_t row_distance(const uint8_t *row, const uint8
                                                  int cpl)
 {
     if constexpr (DT != ANN_I8S) {
-        switch (cpl) {
-        case 8: return group_distance<DT, MT, 8>(row, q, rowbytes, sub, G);
-        case 4: return group_distance<DT, MT, 4>(row, q, rowbytes, sub, G);
-        case 2: return group_distance<DT, MT, 2>(row, q, rowbytes, sub, G);
-        case 1: return group_distance<DT, MT, 1>(row, q, rowbytes, sub, G);
-        default: break;
-        }
+        if (cpl == 8)
+            return group_distance<DT, MT, 8>(row, q, rowbytes, sub, G);
     }
     return group_distance<DT, MT, 0>(row, q, rowbytes, sub, G);
 }
 
+// One TMA tensor gather of four whole base rows (row ids r0..r3) into four
+// consecutive staging rows at dst, counted on bar.
+__device__ __forceinline__ void gather4_rows(void *dst, const CUtensorMap *map, int32_t r0, int32_t r1, int32_t r2,
+                                             int32_t r3, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_addr(dst)),
+        "l"(map), "r"(0), "r"(r0), "r"(r1), "r"(r2), "r"(r3), "r"(smem_addr(bar))
+        : "memory");
+}
+
 template <int DT, int MT>
-__global__ void __launch_bounds__(32 * kMaxSearchWarps, 16) beam_search_kernel(const SearchArgs a)
+__global__ void __launch_bounds__(32 * kMaxSearchWarps, 16) beam_search_kernel(const __grid_constant__ SearchArgs a)
 {
     extern __shared__ __align__(128) uint8_t smem[];
     const int lane = threadIdx.x & 31;
@@ -446,13 +455,28 @@ __global__ void __launch_bounds__(32 * kMaxSearchWarps, 16) beam_search_kernel(c
             if (nc > 0) {
                 for (int c0 = 0; c0 < nc; c0 += a.stage_rows) {
                     const int ch = min(a.stage_rows, nc - c0);
-                    if (lane == 0)
-                        mbar_arrive_expect_tx(bar, static_cast<uint32_t>(ch) * a.rowbytes);
-                    __syncwarp();
-                    for (int j = lane; j < ch; j += 32)
-                        bulk_g2s(stage + j * a.stage_stride,
-                                 a.base + static_cast<size_t>(key_id(cbuf[c0 + j])) * a.rowbytes,
-                                 a.rowbytes, bar);
+                    if (a.gather4) {
+                        // groups of four rows, the last group padded by
+                        // repeating its last row
+                        const int ng = (ch + 3) >> 2;
+                        if (lane == 0)
+                            mbar_arrive_expect_tx(bar, static_cast<uint32_t>(ng) * 4 * a.rowbytes);
+                        __syncwarp();
+                        for (int g = lane; g < ng; g += 32) {
+                            const int j = c0 + 4 * g, last = c0 + ch - 1;
+                            gather4_rows(stage + 4 * g * a.stage_stride, &a.row_map, key_id(cbuf[j]),
+                                         key_id(cbuf[min(j + 1, last)]), key_id(cbuf[min(j + 2, last)]),
+                                         key_id(cbuf[min(j + 3, last)]), bar);
+                        }
+                    } else {
+                        if (lane == 0)
+                            mbar_arrive_expect_tx(bar, static_cast<uint32_t>(ch) * a.rowbytes);
+                        __syncwarp();
+                        for (int j = lane; j < ch; j += 32)
+                            bulk_g2s(stage + j * a.stage_stride,
+                                     a.base + static_cast<size_t>(key_id(cbuf[c0 + j])) * a.rowbytes, a.rowbytes,
+                                     bar);
+                    }
                     const bool ok = !a.fault_wait && mbar_wait_bounded(bar, phase, kTimeoutIters);
                     if (!__all_sync(kFull, ok)) {
                         // the query fails with a timeout; give the copies one
@@ -954,30 +978,41 @@ ann_status launch_search(ann_index *idx, const SearchLaunch &L, cudaStream_t s)
     a.team_lg = 0;
     while ((1 << a.team_lg) < G)
         ++a.team_lg;
+    // gather mode: one TMA tensor gather per four rows when the index has a
+    // row map and the caller asks for it (or leaves it to the default, one
+    // bulk copy per row)
+    a.gather4 = (p->gather == 4 && idx->has_row_map) ? 1 : 0;
+    if (a.gather4)
+        a.row_map = idx->row_map;
     // staging stride in 16-byte units.  A quarter-warp phase of 16-byte loads
     // covers 8 lanes; with G < 8 they read 8 / G rows, whose G-chunk runs hit
-    // distinct banks when the stride is G times an odd number.
+    // distinct banks when the stride is G times an odd number.  Tensor
+    // gathers write four rows back to back, so their stride is the row size.
     int s16 = chunks;
-    if (G < 8)
+    if (G < 8 && !a.gather4)
         while (s16 % G != 0 || ((s16 / G) & 1) == 0)
             ++s16;
     a.stage_stride = s16 * 16;
     a.cpl = 0;
     if (idx->dtype != ANN_I8S && chunks % G == 0) {
         const int c = chunks / G;
-        a.cpl = (c == 1 || c == 2 || c == 4 || c == 8) ? c : 0;
+        a.cpl = c == 8 ? c : 0;
     }
     // Most steps find far fewer new neighbours than W * R (about 30 % of
     // them), so a small staging area filled in rounds keeps shared memory per
     // team small (more teams per SM); at most 48 KB staged at once, which also
     // keeps one mbarrier phase's byte count far below its 2^20 limit.
     a.stage_rows = std::max(1, std::min({maxc, p->stage_rows > 0 ? p->stage_rows : 16, 49152 / a.stage_stride}));
+    if (a.gather4)
+        a.stage_rows = (a.stage_rows + 3) / 4 * 4;  // whole groups of four
 
     size_t off = 16;  // mbarrier
     a.off_sel = static_cast<int>(off);
     off = align_up(off + 4 * 2 * ANN_MAX_W, 16);  // selected and predicted ids
     a.off_q = static_cast<int>(off);
     off = align_up(off + L.qbytes + a.qpad, 16);
+    if (a.gather4)
+        off = align_up(off, 128);  // tensor gathers land on 128-byte boundaries
     a.off_stage = static_cast<int>(off);
     off = align_up(off + static_cast<size_t>(a.stage_rows) * a.stage_stride, 16);
     a.off_pool = static_cast<int>(off);

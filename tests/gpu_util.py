@@ -16,7 +16,7 @@ def make_index(base, graph, medoid, metric=ann.L2, base_f32=None):
 
 
 def search(h, queries, k, L, W=1, entries=None, hash_bits=0, ks=None, Ls=None, targets=None,
-           u8=None, team=0, stage_rows=0, spill_bits=0, flags=0):
+           u8=None, team=0, stage_rows=0, spill_bits=0, flags=0, gather=0):
     q = torch.from_numpy(np.ascontiguousarray(queries)).to(DEV)
     nq = q.shape[0]
     if u8 is None:
@@ -28,7 +28,7 @@ def search(h, queries, k, L, W=1, entries=None, hash_bits=0, ks=None, Ls=None, t
     ent, dk, dL, dt = t(entries), t(ks), t(Ls), t(targets)
     m = 0 if entries is None or np.ndim(entries) == 1 else np.shape(entries)[1]
     p = ann.search_params(k, L, W=W, hash_bits=hash_bits, d_k=dk, d_L=dL, d_target=dt, team=team,
-                          stage_rows=stage_rows, spill_bits=spill_bits, flags=flags, n_entries=m)
+                          stage_rows=stage_rows, spill_bits=spill_bits, flags=flags, n_entries=m, gather=gather)
     ann.ann_search_batch(h, q, nq, ent, p, ids, dists, stats)
     st = ann.ann_sync_status(h)
     return ids.cpu().numpy(), dists.cpu().numpy(), stats[:, 0].cpu().numpy(), \

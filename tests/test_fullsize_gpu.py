@@ -39,8 +39,8 @@ def full():
     ann.ann_free_index(h)
 
 
-def _lanes(full, entries, m):
-    p = ann.search_params(K, L, W=W, hash_bits=-1, stage_rows=8, team=4, n_entries=m)
+def _lanes(full, entries, m, gather=1):
+    p = ann.search_params(K, L, W=W, hash_bits=-1, stage_rows=8, team=4, n_entries=m, gather=gather)
     streams = [torch.cuda.Stream(device=DEV) for _ in range(3)]
     outs = []
     torch.cuda.synchronize()
@@ -64,15 +64,15 @@ def _recall(ids, gt):
     return np.mean([len(set(a) & set(b)) / K for a, b in zip(ids, gt)])
 
 
-@pytest.mark.parametrize("seeds", [0, 2])
-def test_full_size_sampled_parity(full, seeds):
+@pytest.mark.parametrize("seeds,gather", [(0, 1), (2, 1), (0, 4)])
+def test_full_size_sampled_parity(full, seeds, gather):
     rng = np.random.default_rng(11 + seeds)
     if seeds:
         ent_np = rng.integers(0, N, size=(NQ, seeds)).astype(np.int32)
         ent = torch.from_numpy(ent_np).to(DEV)
     else:
         ent_np, ent = None, None
-    ids, dd, st = _lanes(full, ent, seeds)
+    ids, dd, st = _lanes(full, ent, seeds, gather)
     sample = np.sort(rng.choice(NQ, 200, replace=False))
     q64 = full["w"]["queries"][sample].astype(np.float64)
     e = full["med"] if ent_np is None else ent_np[sample]

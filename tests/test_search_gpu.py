@@ -99,12 +99,14 @@ def test_u8_wide_rows_bit_exact(c1, R, W):
     assert np.array_equal(ev, oe) and np.array_equal(hp, oh)
 
 
-@pytest.mark.parametrize("team,stage_rows", [(1, 32), (2, 4), (4, 8), (16, 16), (32, 5)])
-def test_c1_team_sizes_bit_exact(c1, team, stage_rows):
-    # every distance team size and gather round size gives the same exact
-    # int32 distances, hence the same search
+@pytest.mark.parametrize("team,stage_rows,gather", [(1, 32, 1), (2, 4, 1), (4, 8, 1), (16, 16, 1), (32, 5, 1),
+                                                    (4, 8, 4), (8, 5, 4), (2, 12, 4), (32, 16, 4), (4, 1, 4)])
+def test_c1_team_sizes_bit_exact(c1, team, stage_rows, gather):
+    # every distance team size, gather round size and fetch mode (a bulk copy
+    # per row, or TMA tensor gathers of four rows with ragged rounds padded)
+    # gives the same exact int32 distances, hence the same search
     q = c1["queries"]
-    ids, d, ev, hp, st = search(c1["h"], q, 10, 128, W=2, team=team, stage_rows=stage_rows)
+    ids, d, ev, hp, st = search(c1["h"], q, 10, 128, W=2, team=team, stage_rows=stage_rows, gather=gather)
     oi, od, oe, oh = _oracle(c1, q, 128, 10, W=2)
     assert st == ann.OK
     assert np.array_equal(ids, oi) and np.array_equal(ev, oe) and np.array_equal(hp, oh)
@@ -234,10 +236,11 @@ def _f32_parity(ids, d, oi, od, truth, scale=None):
     assert abs(r_gpu - r_or) <= 1e-3
 
 
-@pytest.mark.parametrize("L,W,team", [(32, 1, 0), (64, 1, 0), (128, 2, 0), (128, 2, 2), (128, 4, 32)])
-def test_f32_l2_parity(f32_case, L, W, team):
+@pytest.mark.parametrize("L,W,team,gather", [(32, 1, 0, 0), (64, 1, 0, 0), (128, 2, 0, 0), (128, 2, 2, 0),
+                                            (128, 4, 32, 0), (96, 4, 4, 4), (128, 4, 8, 4)])
+def test_f32_l2_parity(f32_case, L, W, team, gather):
     q = f32_case["queries"]
-    ids, d, ev, hp, st = search(f32_case["h"], q, 10, L, W=W, team=team)
+    ids, d, ev, hp, st = search(f32_case["h"], q, 10, L, W=W, team=team, gather=gather)
     oi, od, oe, oh = _oracle(f32_case, q, L, 10, W=W)
     truth, _ = oracle.knn(f32_case["base"], q.astype(np.float64), 10)
     assert st == ann.OK
