@@ -188,8 +188,8 @@ def parse():
     ap.add_argument("--fixed-L", type=int, default=0,
                     help="skip the L sweep and run every entry mode at this pool size")
     ap.add_argument("--knobs", default="",
-                    help="fixed search sizes hash_bits,stage_rows,team,spill_bits,gather instead of ann_autotune "
-                         "(for a profiler capture of one known configuration)")
+                    help="fixed search sizes hash_bits,stage_rows,team,spill_bits,gather[,visited_l2] instead of "
+                         "ann_autotune (for a profiler capture of one known configuration)")
     ap.add_argument("--alpha", type=float, default=1.0,
                     help="RNG pruning factor of the graph builder (c is dropped when a kept s has "
                          "alpha * d(s, c) <= d(p, c); above 1 keeps more long edges)")
@@ -567,6 +567,7 @@ class Runner:
         self.tuned[L] = best
         return {"hash_bits": best.hash_bits, "stage_rows": best.stage_rows, "team": best.team,
                 "spill_bits": best.spill_bits, "gather": best.gather,
+                "visited_l2": bool(best.flags & self.ann.SEARCH_VISITED_L2),
                 "search_ms": ms}
 
     def select(self, q):
@@ -602,8 +603,11 @@ def sweep(run, torch, ann, W, targets):
     def measure(L):
         run.step(L, stats=True)
         st = ann.ann_sync_status(run.h, run.stream)
-        if st != ann.OK:
+        # a query that outgrows the visited tables fails alone (ids -1) and
+        # counts as no hit; any other device error ends the run
+        if st not in (ann.OK, ann.ERR_CAPACITY):
             raise RuntimeError(f"search at L={L} reported: {ann.status_string(st)}")
+        failed = int((run.ids[:, 0] < 0).sum().item()) if st == ann.ERR_CAPACITY else 0
         r = recall(run.ids.cpu().numpy(), W["gt"], run.k)
         s = run.stats.cpu().numpy()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -612,8 +616,12 @@ def sweep(run, torch, ann, W, targets):
             run.step(L)
         e1.record(run.stream)
         torch.cuda.synchronize()
-        return dict(L=L, recall=r, evals=float(s[:, 0].mean()), hops=float(s[:, 1].mean()),
-                    qps=run.nq * 5 / (e0.elapsed_time(e1) / 1e3))
+        out = dict(L=L, recall=r, evals=float(s[:, 0].mean()), hops=float(s[:, 1].mean()),
+                   qps=run.nq * 5 / (e0.elapsed_time(e1) / 1e3))
+        if failed:
+            out["capacity_failures"] = failed
+            ann.ann_sync_status(run.h, run.stream)  # the timed repeats fail the same queries
+        return out
 
     out = []
     top = max(targets)
@@ -780,11 +788,14 @@ def measure_mode(run, torch, ann, W, args, targets):
     else:
         Lstar, sw, per = sweep(run, torch, ann, W, targets)
     if args.knobs:
-        hb, sr, tm, sb, ga = (int(x) for x in args.knobs.split(","))
+        hb, sr, tm, sb, ga, vl = (int(x) for x in (args.knobs + ",0").split(",")[:6])
         p = run.params(Lstar)
         p.hash_bits, p.stage_rows, p.team, p.spill_bits, p.gather = hb, sr, tm, sb, ga
+        if vl:
+            p.flags |= ann.SEARCH_VISITED_L2
         run.tuned[Lstar] = p
-        tune = {"hash_bits": hb, "stage_rows": sr, "team": tm, "spill_bits": sb, "gather": ga, "fixed": True}
+        tune = {"hash_bits": hb, "stage_rows": sr, "team": tm, "spill_bits": sb, "gather": ga,
+                "visited_l2": bool(vl), "fixed": True}
     else:
         tune = None if args.no_tune else run.autotune(Lstar)
     run.step(Lstar, stats=True)
@@ -917,7 +928,7 @@ def batch_report(W, torch, ann, args, dev, modes):
         for b0 in range(0, nq, B):
             sl = slice(b0, b0 + B)
             pb = ann.search_params(100, 512, W=args.W, hash_bits=best.hash_bits, stage_rows=best.stage_rows,
-                                   team=best.team, spill_bits=best.spill_bits, gather=best.gather, d_k=kq[sl], d_L=Lq[sl],
+                                   team=best.team, spill_bits=best.spill_bits, gather=best.gather, flags=best.flags, d_k=kq[sl], d_L=Lq[sl],
                                    n_entries=ns)
             a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
@@ -929,7 +940,7 @@ def batch_report(W, torch, ann, args, dev, modes):
         ib = torch.empty((B, 100), dtype=torch.int32, device=dev)
         db = torch.empty((B, 100), dtype=torch.float32, device=dev)
         pp = ann.search_params(100, 512, W=args.W, hash_bits=best.hash_bits, stage_rows=best.stage_rows,
-                               team=best.team, spill_bits=best.spill_bits, gather=best.gather, d_k=kb, d_L=lb, n_entries=ns)
+                               team=best.team, spill_bits=best.spill_bits, gather=best.gather, flags=best.flags, d_k=kb, d_L=lb, n_entries=ns)
         plan = ann.ann_plan_create(W["h"], qb, B, em, args.l_hub, pp, None if em == ann.ENTRY_MEDOID else eb,
                                    ib, db)
         try:
@@ -946,7 +957,8 @@ def batch_report(W, torch, ann, args, dev, modes):
             "qps_one_launch": qps, "recall_at_own_k": rec, "queries": nq,
             "evals_per_query": float(s[:, 0].mean()), "hops_per_query": float(s[:, 1].mean()),
             "tuned": {"hash_bits": best.hash_bits, "stage_rows": best.stage_rows, "team": best.team,
-                      "spill_bits": best.spill_bits, "gather": best.gather},
+                      "spill_bits": best.spill_bits, "gather": best.gather,
+                      "visited_l2": bool(best.flags & ann.SEARCH_VISITED_L2)},
             "batch": B, "batch_latency_ms": {"p50": float(np.percentile(lat, 50)),
                                              "p99": float(np.percentile(lat, 99))},
             "plan_latency_ms": {"p50": float(np.percentile(lat_plan, 50)),

@@ -60,6 +60,7 @@ typedef struct ann_index ann_index;
 /* Search flags */
 #define ANN_SEARCH_RERANK 1u /* re-score the final pool from the fp32 copy (see ann_index_desc.base_f32) */
 #define ANN_SEARCH_FAULT_WAIT 2u /* fault injection for tests of the timeout path (see ann_search_params) */
+#define ANN_SEARCH_VISITED_L2 4u /* keep the first-level visited tables resident in L2 (see ann_search_params) */
 
 /* Limits of one search */
 #define ANN_MAX_L 4096     /* pool size L */
@@ -132,6 +133,14 @@ typedef struct {
  *             it the call returns ANN_ERR_UNSUPPORTED) and the k best by
  *             (fp32 distance, id) are returned (the precision line: reduced-
  *             precision storage for traversal, exact scores for the answer).
+ *             ANN_SEARCH_VISITED_L2 (speed only): when the first-level visited
+ *             tables of all the launch's teams fit the device's persisting-L2
+ *             capacity, the search launches with an access-policy window that
+ *             keeps them resident in L2 (no write-back, and compare-and-swaps
+ *             that hit in L2); otherwise it launches without one.  The first
+ *             such call on a device outside stream capture raises the
+ *             context's persisting-L2 limit (cudaLimitPersistingL2CacheSize)
+ *             to the device maximum; the limit ends with the process.
  *             ANN_SEARCH_FAULT_WAIT: fault injection for testing; every wait
  *             for a round of gathered rows gives up at once, as if its time
  *             limit had passed: each query fails with -1 ids and the call

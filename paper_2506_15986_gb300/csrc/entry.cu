@@ -376,7 +376,7 @@ __global__ void map_hub_seeds(const int32_t *hub_ids, int64_t nq, int m, const i
 // stops when no unexpanded entry is left.  The m best pool entries become the
 // seeds (their hubs' nodes).
 constexpr int kNavWarps = 8;
-constexpr int kNavMaxPool = 32;
+constexpr int kNavMaxPool = 64;
 
 __device__ __forceinline__ float hub_score(const float *q, const __nv_bfloat16 *row)
 {
@@ -404,6 +404,27 @@ __device__ __forceinline__ float hub_score(const float *q, const __nv_bfloat16 *
     return -((a0 + a1) + (a2 + a3));
 }
 
+// Keys of lanes [0, 32) ascending: the 32 smallest of a (ascending, one key
+// per lane) and b (ascending) in *lo, the 32 largest in *hi.  Pairwise minima
+// of a against b reversed form a bitonic sequence (the maxima another), which
+// five half-cleaner stages sort.
+__device__ __forceinline__ void merge32(uint64_t a, uint64_t b, int lane, uint64_t *lo, uint64_t *hi)
+{
+    const uint64_t rb = __shfl_sync(kFull, b, 31 - lane);
+    uint64_t mn = a < rb ? a : rb, mx = a < rb ? rb : a;
+#pragma unroll
+    for (int j = 16; j > 0; j >>= 1) {
+        const uint64_t o = __shfl_xor_sync(kFull, mn, j), p = __shfl_xor_sync(kFull, mx, j);
+        mn = (lane & j) ? kmax(mn, o) : kmin(mn, o);
+        mx = (lane & j) ? kmax(mx, p) : kmin(mx, p);
+    }
+    *lo = mn;
+    *hi = mx;
+}
+
+// NP keys per lane: pools of up to 32 * NP hubs (element r * 32 + lane in
+// pool[r]).
+template <int NP>
 __global__ void __launch_bounds__(32 * kNavWarps, 4)
     hub_nav_kernel(const float *qhat, int64_t nq, const __nv_bfloat16 *Eb, int H, const int32_t *hgraph, int s,
                    int32_t entry, int L, int m_seeds, const int32_t *hub_nodes, int32_t medoid, int bm_words,
@@ -422,19 +443,37 @@ __global__ void __launch_bounds__(32 * kNavWarps, 4)
             vis[w] = 0u;
         __syncwarp();
         // the initial pool: the entry hub, evaluated
-        uint64_t pool = kKeyMax;
+        uint64_t pool[NP];
+#pragma unroll
+        for (int r = 0; r < NP; ++r)
+            pool[r] = kKeyMax;
         if (lane == 0) {
             vis[entry >> 5] = 1u << (entry & 31);
-            pool = make_key(f32_to_ord(hub_score(q, Eb + static_cast<int64_t>(entry) * 64)), entry);
+            pool[0] = make_key(f32_to_ord(hub_score(q, Eb + static_cast<int64_t>(entry) * 64)), entry);
         }
         for (;;) {
-            const unsigned um = __ballot_sync(kFull, lane < L && pool != kKeyMax && !(pool & 1ull));
-            if (!um)
+            // the first unexpanded entry in pool order
+            int f = -1, fr = 0;
+#pragma unroll
+            for (int r = NP - 1; r >= 0; --r) {
+                const unsigned um =
+                    __ballot_sync(kFull, r * 32 + lane < L && pool[r] != kKeyMax && !(pool[r] & 1ull));
+                if (um) {
+                    f = __ffs(um) - 1;
+                    fr = r;
+                }
+            }
+            if (f < 0)
                 break;
-            const int f = __ffs(um) - 1;
-            if (lane == f)
-                pool |= 1ull;
-            const int32_t node = __shfl_sync(kFull, key_id(pool), f);
+            int32_t node = 0;
+#pragma unroll
+            for (int r = 0; r < NP; ++r) {
+                if (r == fr && lane == f)
+                    pool[r] |= 1ull;
+                const int32_t v = __shfl_sync(kFull, key_id(pool[r]), f);
+                if (r == fr)
+                    node = v;
+            }
             __syncwarp();
             const int32_t nb = lane < s ? __ldg(hgraph + static_cast<int64_t>(node) * s + lane) : -1;
             uint64_t cand = kKeyMax;
@@ -444,20 +483,20 @@ __global__ void __launch_bounds__(32 * kNavWarps, 4)
                     cand = make_key(f32_to_ord(hub_score(q, Eb + static_cast<int64_t>(nb) * 64)), nb);
             }
             cand = warp_sort32(cand, lane);
-            // the 32 smallest of two ascending sequences: pairwise minima of
-            // one against the other reversed form a bitonic sequence, which
-            // five half-cleaner stages sort
-            const uint64_t rc = __shfl_sync(kFull, cand, 31 - lane);
-            uint64_t mn = pool < rc ? pool : rc;
+            // the pool keeps the L smallest keys of itself and the new ones:
+            // merge the new keys into the lower 32, the displaced ones into
+            // the next 32 (every key of pool[r + 1] is above every key of pool[r])
+            uint64_t carry = cand;
 #pragma unroll
-            for (int j = 16; j > 0; j >>= 1) {
-                const uint64_t o = __shfl_xor_sync(kFull, mn, j);
-                mn = (lane & j) ? kmax(mn, o) : kmin(mn, o);
+            for (int r = 0; r < NP; ++r) {
+                uint64_t lo, hi;
+                merge32(pool[r], carry, lane, &lo, &hi);
+                pool[r] = r * 32 + lane < L ? lo : kKeyMax;
+                carry = hi;
             }
-            pool = lane < L ? mn : kKeyMax;
         }
         if (lane < m_seeds) {
-            const int32_t hub = pool != kKeyMax ? key_id(pool) : -1;
+            const int32_t hub = pool[0] != kKeyMax ? key_id(pool[0]) : -1;
             out[qi * m_seeds + lane] = hub >= 0 ? hub_nodes[hub] : (lane == 0 ? medoid : -1);
         }
         __syncwarp();
@@ -785,16 +824,17 @@ ann_status ann_select_entries(ann_index *idx, const void *d_queries, int64_t nq,
         const Operand Q{qbf, OP_BF16, 64, 1, nq, 64, nullptr};
         st = launch_hub_argmax(m, Q, nq, d_entry, hid, hsc, idx->d_status, s, m_seeds);
     } else if (st == ANN_OK && L_hub <= kNavMaxPool && m->s <= 32) {
-        // the hub-graph search in one launch (pools of up to 32 hubs)
+        // the hub-graph search in one launch (pools of up to 64 hubs)
         const int bm_words = (m->H + 127) / 128 * 4;
         const size_t per_warp = 256 + 4 * static_cast<size_t>(bm_words);
         const size_t smem = per_warp * kNavWarps;
-        cudaError_t e = cudaFuncSetAttribute(hub_nav_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(smem));
+        auto kern = L_hub <= 32 ? hub_nav_kernel<1> : hub_nav_kernel<2>;
+        cudaError_t e =
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
         if (e == cudaSuccess) {
             const int64_t blocks = std::min<int64_t>((nq + kNavWarps - 1) / kNavWarps,
                                                      static_cast<int64_t>(idx->num_sms) * 8);
-            hub_nav_kernel<<<static_cast<unsigned>(blocks), 32 * kNavWarps, smem, s>>>(
+            kern<<<static_cast<unsigned>(blocks), 32 * kNavWarps, smem, s>>>(
                 qhat, nq, m->Eb, m->H, m->hub_graph, m->s, m->hub_entry, L_hub, m_seeds, m->hub_nodes, idx->medoid,
                 bm_words, d_entry);
             e = cudaGetLastError();

@@ -145,7 +145,7 @@ ann_status ann_autotune(ann_index *idx, const void *d_queries, int64_t nq, const
     for (int hb = hb0 - 3; hb <= hb0; ++hb)
         if (hb >= 8 && hb <= 15)
             hbs.push_back(hb);
-    const int srs[] = {4, 8, 12, 16};
+    const int srs[] = {4, 6, 8, 12, 16};
     float bms = 1e30f;
     ann_search_params bp = *p;
     // times one candidate: reps batches, batch r on lane r mod lanes; false on
@@ -235,6 +235,22 @@ ann_status ann_autotune(ann_index *idx, const void *d_queries, int64_t nq, const
                 c.team = teams[ti];
                 ok = trial(c);
             }
+        }
+    }
+    // stage 5: first-level visited tables kept resident in L2 (applied by
+    // the launch only when they fit the persisting-L2 capacity), at the best
+    // table size so far and one and two sizes smaller (smaller tables fit
+    // more often; their longer probe chains then hit in L2)
+    {
+        const ann_search_params b4 = bp;
+        const int sbb = b4.spill_bits > 0 ? b4.spill_bits : ann::default_spill_bits(p->L);
+        for (int sb = sbb; ok && sb >= sbb - 2; --sb) {
+            if (sb < 10 || sb > 16)
+                continue;
+            ann_search_params c = b4;
+            c.flags |= ANN_SEARCH_VISITED_L2;
+            c.spill_bits = sb;
+            ok = trial(c);
         }
     }
     // the caller's outputs hold the chosen combination's results

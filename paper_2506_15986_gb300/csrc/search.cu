@@ -29,6 +29,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "device_util.cuh"
 #include "internal.h"
@@ -44,6 +45,7 @@ constexpr int kSlots = ANN_MAX_STEP_CAND / 32;  // neighbour slots per lane in o
 struct SearchArgs {
     CUtensorMap row_map;  // four-row TMA gathers of base rows (gather4 only)
     int gather4;          // 1: a round's rows come in TMA tensor gathers of four
+    int nteams;           // teams of the launch (the first-level tables come first in the scratch)
     const uint8_t *base;
     const int32_t *graph;
     int64_t n;
@@ -371,9 +373,12 @@ __global__ void __launch_bounds__(32 * kMaxSearchWarps, 16) beam_search_kernel(c
     uint32_t *htab = reinterpret_cast<uint32_t *>(my + a.off_hash);
     const int team = blockIdx.x * (blockDim.x >> 5) + wid;
     // two global spill tables per team: 2^spill_bits slots, then one four
-    // times larger for the rare query that outgrows the first
-    uint32_t *gtab1 = a.spill + static_cast<size_t>(team) * (static_cast<size_t>(5) << a.spill_bits);
-    uint32_t *gtab2 = gtab1 + (static_cast<size_t>(1) << a.spill_bits);
+    // times larger for the rare query that outgrows the first; the first
+    // tables of all teams lie together at the front of the scratch (one
+    // range for an L2 access-policy window), the larger ones after them
+    uint32_t *gtab1 = a.spill + static_cast<size_t>(team) * (static_cast<size_t>(1) << a.spill_bits);
+    uint32_t *gtab2 = a.spill + static_cast<size_t>(a.nteams) * (static_cast<size_t>(1) << a.spill_bits) +
+                      static_cast<size_t>(team) * (static_cast<size_t>(4) << a.spill_bits);
 
     if (lane == 0) {
         mbar_init(bar, 1);
@@ -873,11 +878,54 @@ ann_status teams_for(ann_index *idx, size_t per_warp, int *teams, int *wpc)
     return ANN_OK;
 }
 
+// window: bytes of the first-level visited tables to keep resident in L2
+// (0 = launch without an access-policy window), at the given hit ratio
 template <int DT, int MT>
-ann_status launch_typed(const SearchArgs &a, size_t smem, int teams, int wpc, cudaStream_t s)
+ann_status launch_typed(const SearchArgs &a, size_t smem, int teams, int wpc, cudaStream_t s, size_t window,
+                        float hit_ratio)
 {
-    beam_search_kernel<DT, MT><<<teams / wpc, 32 * wpc, smem, s>>>(a);
-    return cuda_status(cudaGetLastError());
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(teams / wpc);
+    cfg.blockDim = dim3(32 * wpc);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeAccessPolicyWindow;
+    at[0].val.accessPolicyWindow.base_ptr = a.spill;
+    at[0].val.accessPolicyWindow.num_bytes = window;
+    at[0].val.accessPolicyWindow.hitRatio = hit_ratio;
+    at[0].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+    at[0].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+    cfg.attrs = at;
+    cfg.numAttrs = window > 0 ? 1 : 0;
+    return cuda_status(cudaLaunchKernelEx(&cfg, beam_search_kernel<DT, MT>, a));
+}
+
+// Bytes of L2 the first-level visited tables may keep resident on the
+// current device: the device's persisting-L2 maximum, to which the context's
+// limit is raised once (outside stream capture) for ANN_SEARCH_VISITED_L2.
+size_t persisting_l2_bytes(int dev, cudaStream_t s)
+{
+    constexpr int kMaxDevices = 64;
+    static std::atomic<int> raised[kMaxDevices];
+    if (dev < 0 || dev >= kMaxDevices)
+        return 0;
+    int maxp = 0;
+    if (cudaDeviceGetAttribute(&maxp, cudaDevAttrMaxPersistingL2CacheSize, dev) != cudaSuccess || maxp <= 0)
+        return 0;
+    size_t cur = 0;
+    if (cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize) != cudaSuccess)
+        return 0;
+    if (cur < static_cast<size_t>(maxp) && !raised[dev].load()) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone &&
+            cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, static_cast<size_t>(maxp)) == cudaSuccess) {
+            raised[dev].store(1);
+            cur = static_cast<size_t>(maxp);
+        }
+        cudaGetLastError();
+    }
+    return cur;
 }
 
 #define ANN_DISPATCH(FN, ...)                                                        \
@@ -1051,6 +1099,7 @@ ann_status launch_search(ann_index *idx, const SearchLaunch &L, cudaStream_t s)
         return ANN_ERR_CAPACITY;
     }
     a.counter = static_cast<unsigned long long *>(scratch);
+    a.nteams = teams;
     a.spill = reinterpret_cast<uint32_t *>(static_cast<uint8_t *>(scratch) + 256);
     // exact rerank: the search hands its whole pool to rerank_kernel
     const bool rerank = (p->flags & ANN_SEARCH_RERANK) != 0;
@@ -1064,9 +1113,20 @@ ann_status launch_search(ann_index *idx, const SearchLaunch &L, cudaStream_t s)
         }
         a.pool_out = static_cast<int32_t *>(pool_buf);
     }
+    // L2-resident first-level visited tables, when asked for and they fit
+    size_t window = 0;
+    float hit_ratio = 1.f;
+    if (p->flags & ANN_SEARCH_VISITED_L2) {
+        const size_t tbytes = static_cast<size_t>(teams) * (static_cast<size_t>(4) << a.spill_bits);
+        int maxwin = 0;
+        cudaDeviceGetAttribute(&maxwin, cudaDevAttrMaxAccessPolicyWindowSize, idx->device);
+        const size_t setaside = persisting_l2_bytes(idx->device, s);
+        if (tbytes <= setaside && tbytes <= static_cast<size_t>(maxwin))
+            window = tbytes;
+    }
     cudaError_t e = cudaMemsetAsync(scratch, 0, 8, s);
     if (e == cudaSuccess) {
-        ANN_DISPATCH(launch_typed, a, smem, teams, wpc, s);
+        ANN_DISPATCH(launch_typed, a, smem, teams, wpc, s, window, hit_ratio);
     } else {
         st = cuda_status(e);
     }

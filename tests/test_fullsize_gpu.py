@@ -39,8 +39,9 @@ def full():
     ann.ann_free_index(h)
 
 
-def _lanes(full, entries, m, gather=1):
-    p = ann.search_params(K, L, W=W, hash_bits=-1, stage_rows=8, team=4, n_entries=m, gather=gather)
+def _lanes(full, entries, m, gather=1, l2=False):
+    p = ann.search_params(K, L, W=W, hash_bits=-1, stage_rows=8, team=4, n_entries=m, gather=gather,
+                          spill_bits=12 if l2 else 0, flags=ann.SEARCH_VISITED_L2 if l2 else 0)
     streams = [torch.cuda.Stream(device=DEV) for _ in range(3)]
     outs = []
     torch.cuda.synchronize()
@@ -64,15 +65,17 @@ def _recall(ids, gt):
     return np.mean([len(set(a) & set(b)) / K for a, b in zip(ids, gt)])
 
 
-@pytest.mark.parametrize("seeds,gather", [(0, 1), (2, 1), (0, 4)])
-def test_full_size_sampled_parity(full, seeds, gather):
+@pytest.mark.parametrize("seeds,gather,l2", [(0, 1, False), (2, 1, False), (0, 4, True)])
+def test_full_size_sampled_parity(full, seeds, gather, l2):
+    # l2: the tuned headline's 2^12-slot first-level visited tables kept
+    # resident in L2 (ANN_SEARCH_VISITED_L2)
     rng = np.random.default_rng(11 + seeds)
     if seeds:
         ent_np = rng.integers(0, N, size=(NQ, seeds)).astype(np.int32)
         ent = torch.from_numpy(ent_np).to(DEV)
     else:
         ent_np, ent = None, None
-    ids, dd, st = _lanes(full, ent, seeds, gather)
+    ids, dd, st = _lanes(full, ent, seeds, gather, l2)
     sample = np.sort(rng.choice(NQ, 200, replace=False))
     q64 = full["w"]["queries"][sample].astype(np.float64)
     e = full["med"] if ent_np is None else ent_np[sample]

@@ -143,6 +143,19 @@ def test_c1_spill_to_global_table_stays_exact(c1, L, spill_bits, hash_bits):
     assert np.array_equal(ids, oi) and np.array_equal(ev, oe) and np.array_equal(hp, oh)
 
 
+@pytest.mark.parametrize("spill_bits", [10, 12])
+def test_visited_tables_kept_in_l2_change_nothing(c1, spill_bits):
+    # ANN_SEARCH_VISITED_L2 only changes where the first-level visited tables
+    # live in the cache: the search stays bit-exact
+    q = c1["queries"]
+    ids, d, ev, hp, st = search(c1["h"], q, 10, 96, W=2, hash_bits=-1, spill_bits=spill_bits,
+                                flags=ann.SEARCH_VISITED_L2)
+    oi, od, oe, oh = _oracle(c1, q, 96, 10, W=2)
+    assert st == ann.OK
+    assert np.array_equal(ids, oi) and np.array_equal(ev, oe) and np.array_equal(hp, oh)
+    assert np.array_equal(d, od.astype(np.int64).astype(np.int32))
+
+
 def test_c1_per_query_entries_k_L(c1):
     rng = np.random.default_rng(3)
     q = c1["queries"]
