@@ -272,6 +272,196 @@ __global__ void __launch_bounds__(128)
     }
 }
 
+// ---- exhaustive entry selection in one kernel ----------------------------------
+
+// The query tower and the exhaustive hub scores with the top-M epilogue for
+// 128 queries per CTA: GEMM 1 and GEMM 2 of the tower as in
+// tower_forward_kernel, q_hat written as BF16 straight into the canonical A
+// tile of the hub GEMM (never through global memory), then the hubs in tiles
+// of 256 with two B buffers and two TMEM accumulators, so that one tile's
+// epilogue overlaps the next tile's staging and MMA.  Scores, ties and the
+// top-M rule are those of hub_argmax_kernel.
+//   shared memory: sA 16 KB (GEMM 1 A chunks, then the q_hat tile), sB 32 KB
+//   (GEMM 1 B chunks, then W2^T), sH 64 KB (the hidden layer, then the two
+//   256 x 64 hub tiles); 120 KB in all keeps one CTA per SM, which owns all
+//   512 TMEM columns.
+constexpr int kEntrySmem = 120 * 1024;
+
+template <int M>
+__global__ void __launch_bounds__(128)
+    entry_exhaustive_kernel(const TowerArgs t, const __nv_bfloat16 *Eb, int H, const int32_t *hub_nodes,
+                            int32_t *out_node)
+{
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t *sA = smem;
+    uint8_t *sB = smem + 16384;
+    uint8_t *sH = smem + 49152;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 114688);  // bar[0], bar[1]
+    uint32_t *slot = reinterpret_cast<uint32_t *>(smem + 114688 + 16);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m = warp * 32 + lane;
+    const int64_t r0 = static_cast<int64_t>(blockIdx.x) * 128;
+    const int64_t row = r0 + m;
+    const bool live = row < t.nq;
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    if (warp == 0)
+        tmem_alloc(slot, 512);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *slot;
+    const uint32_t my_lane = tmem + (static_cast<uint32_t>(warp * 32) << 16);
+    uint32_t ph[2] = {0u, 0u};
+
+    // ---- the tower: GEMM 1, bias + ReLU to BF16, GEMM 2, normalisation
+    const Operand W1{t.W1t, OP_BF16, t.in_dim, 1, 256, t.in_dim, nullptr};
+    bool ok = tc_gemm_tile<256>(t.X, r0, W1, 0, t.in_dim, sA, sB, &bar[0], ph[0], tmem);
+    if (ok) {
+        for (int c0 = 0; c0 < 256; c0 += 32) {
+            float v[32];
+            tmem_ld32(my_lane + c0, v);
+#pragma unroll
+            for (int j = 0; j < 32; j += 8) {
+                float a[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    a[u] = fmaxf(v[j + u] + t.b1[c0 + j + u], 0.f);
+                *reinterpret_cast<uint4 *>(sH + canon_off(m, c0 + j, 32)) = pack8_bf16(a);
+            }
+        }
+        const Operand W2{t.W2t, OP_BF16, 256, 1, 64, 256, nullptr};
+        stage_tile<64, 32>(sB, W2, 0, 0);
+        fence_proxy_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            tc_fence_after();
+            constexpr uint32_t ID2 = idesc_bf16_f32(128, 64);
+#pragma unroll
+            for (int kk = 0; kk < 16; ++kk)
+                tc_mma(tmem, smem_desc(sH + kk * 256, 128, 4096), smem_desc(sB + kk * 256, 128, 4096), ID2,
+                       kk > 0 ? 1u : 0u);
+            tc_commit(&bar[0]);
+        }
+        ok = tc_wait(&bar[0], ph[0]);
+    }
+    if (ok) {
+        float z[64];
+        float v[32];
+        tmem_ld32(my_lane, v);
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+            z[j] = v[j] + t.b2[j];
+        tmem_ld32(my_lane + 32, v);
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+            z[32 + j] = v[j] + t.b2[32 + j];
+        float ss = 0.f;
+#pragma unroll
+        for (int j = 0; j < 64; ++j)
+            ss = fmaf(z[j], z[j], ss);
+        const float nrm = sqrtf(ss);
+        const float inv = nrm > 0.f ? 1.0f / nrm : 0.f;
+#pragma unroll
+        for (int j = 0; j < 64; ++j)
+            z[j] *= inv;
+        if (live && t.qhat) {
+            float4 *dst = reinterpret_cast<float4 *>(t.qhat + row * 64);
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                dst[j] = make_float4(z[4 * j], z[4 * j + 1], z[4 * j + 2], z[4 * j + 3]);
+        }
+        // q_hat as the A operand of the hub GEMM (rows past nq hold zeros'
+        // embeddings and are never written out)
+#pragma unroll
+        for (int j = 0; j < 64; j += 8)
+            *reinterpret_cast<uint4 *>(sA + canon_off(m, j, 8)) = pack8_bf16(z + j);
+    }
+
+    // ---- hub scores in tiles of 256, double buffered
+    float best[M];
+    int bi[M];
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+        best[j] = -INFINITY;
+        bi[j] = -1;
+    }
+    const Operand E{Eb, OP_BF16, 64, 1, H, 64, nullptr};
+    const int ntiles = (H + 255) / 256;
+    constexpr uint32_t IDH = idesc_bf16_f32(128, 256);
+    auto issue = [&](int tile) {
+        // stage hub tile `tile` into buffer tile & 1 and start its MMA into
+        // accumulator tile & 1 (columns 256 * (tile & 1))
+        uint8_t *b = sH + (tile & 1) * 32768;
+        stage_tile<256, 8>(b, E, static_cast<int64_t>(tile) * 256, 0);
+        fence_proxy_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            tc_fence_after();
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+                tc_mma(tmem + (tile & 1) * 256, smem_desc(sA + kk * 256, 128, 1024), smem_desc(b + kk * 256, 128, 1024),
+                       IDH, kk > 0 ? 1u : 0u);
+            tc_commit(&bar[tile & 1]);
+        }
+    };
+    if (ok) {
+        tc_fence_before();
+        __syncthreads();  // the hidden layer in sH is no longer read by GEMM 2 (waited above)
+        issue(0);
+    }
+    for (int tile = 0; tile < ntiles && ok; ++tile) {
+        if (tile + 1 < ntiles)
+            issue(tile + 1);  // overlaps this tile's wait and epilogue
+        if (!(ok = tc_wait(&bar[tile & 1], ph[tile & 1])))
+            break;
+        const int c0 = tile * 256;
+        for (int cc = 0; cc < 256 && c0 + cc < H; cc += 32) {
+            float v[32];
+            tmem_ld32(my_lane + (tile & 1) * 256 + cc, v);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int col = c0 + cc + j;
+                if (col < H && v[j] > best[M - 1]) {  // strict: the first of equal scores wins
+                    float sv = v[j];
+                    int si = col;
+#pragma unroll
+                    for (int u = 0; u < M; ++u) {
+                        if (sv > best[u]) {
+                            const float tv = best[u];
+                            const int ti = bi[u];
+                            best[u] = sv;
+                            bi[u] = si;
+                            sv = tv;
+                            si = ti;
+                        }
+                    }
+                }
+            }
+        }
+        tc_fence_before();  // these TMEM reads end before the MMA that reuses the accumulator
+    }
+    if (!ok && threadIdx.x == 0)
+        atomicOr(t.status, kStatusTimeoutBit);
+    if (live) {
+#pragma unroll
+        for (int j = 0; j < M; ++j)
+            out_node[row * M + j] = (ok && bi[j] >= 0) ? hub_nodes[bi[j]] : -1;
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 512);
+    }
+}
+
 // ---- model preparation ------------------------------------------------------
 
 // BF16 transposed weight copies for K-major B operands, and normalised hub
@@ -609,6 +799,47 @@ ann_status launch_hub_argmax(const ann_entry_model *m, const Operand &Q, int64_t
     }
 }
 
+template <int M>
+ann_status launch_entry_topm(const ann_entry_model *m, const Operand &X, int64_t nq, float *qhat, int32_t *out_node,
+                             int *status, cudaStream_t s)
+{
+    TowerArgs t{};
+    t.X = X;
+    t.W1t = m->W1t;
+    t.in_dim = m->in_dim;
+    t.b1 = m->b1;
+    t.W2t = m->W2t;
+    t.b2 = m->b2;
+    t.nq = nq;
+    t.qhat = qhat;
+    t.status = status;
+    cudaError_t e = cudaFuncSetAttribute(entry_exhaustive_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kEntrySmem);
+    if (e != cudaSuccess)
+        return cuda_status(e);
+    entry_exhaustive_kernel<M><<<static_cast<unsigned>((nq + 127) / 128), 128, kEntrySmem, s>>>(
+        t, m->Eb, m->H, m->hub_nodes, out_node);
+    return cuda_status(cudaGetLastError());
+}
+
+ann_status launch_entry_exhaustive(const ann_entry_model *m, const Operand &X, int64_t nq, float *qhat,
+                                   int32_t *out_node, int topm, int *status, cudaStream_t s)
+{
+    if (nq == 0)
+        return ANN_OK;
+    switch (topm) {
+    case 1: return launch_entry_topm<1>(m, X, nq, qhat, out_node, status, s);
+    case 2: return launch_entry_topm<2>(m, X, nq, qhat, out_node, status, s);
+    case 3: return launch_entry_topm<3>(m, X, nq, qhat, out_node, status, s);
+    case 4: return launch_entry_topm<4>(m, X, nq, qhat, out_node, status, s);
+    case 5: return launch_entry_topm<5>(m, X, nq, qhat, out_node, status, s);
+    case 6: return launch_entry_topm<6>(m, X, nq, qhat, out_node, status, s);
+    case 7: return launch_entry_topm<7>(m, X, nq, qhat, out_node, status, s);
+    case 8: return launch_entry_topm<8>(m, X, nq, qhat, out_node, status, s);
+    default: return ANN_ERR_INVALID_ARG;
+    }
+}
+
 ann_status build_hub_index(ann_index *idx, ann_entry_model *m, const int32_t *hub_graph, int32_t hub_entry,
                            cudaStream_t s)
 {
@@ -805,6 +1036,14 @@ ann_status ann_select_entries(ann_index *idx, const void *d_queries, int64_t nq,
         cudaSetDevice(prev);
         return m ? ANN_ERR_INVALID_ARG : ANN_ERR_UNSUPPORTED;
     }
+    const Operand X{d_queries, idx->dtype == ANN_U8 ? OP_U8 : OP_F32, idx->dim, 1, nq, idx->dim, nullptr};
+    if (mode == ANN_ENTRY_LEARNED_EXHAUSTIVE) {
+        // the tower, the hub scores and the top-m in one launch, q_hat kept
+        // in shared memory: no scratch
+        st = launch_entry_exhaustive(m, X, nq, d_qhat, d_entry, m_seeds, idx->d_status, s);
+        cudaSetDevice(prev);
+        return st;
+    }
     // scratch: q_hat fp32 + bf16, hub ids, hub scores
     const size_t qf = static_cast<size_t>(nq) * 64 * 4, qb = static_cast<size_t>(nq) * 64 * 2;
     const size_t hb = static_cast<size_t>(nm) * 4;
@@ -818,12 +1057,8 @@ ann_status ann_select_entries(ann_index *idx, const void *d_queries, int64_t nq,
     __nv_bfloat16 *qbf = reinterpret_cast<__nv_bfloat16 *>(static_cast<uint8_t *>(scr) + qf);
     int32_t *hid = reinterpret_cast<int32_t *>(static_cast<uint8_t *>(scr) + qf + qb);
     float *hsc = reinterpret_cast<float *>(static_cast<uint8_t *>(scr) + qf + qb + hb);
-    const Operand X{d_queries, idx->dtype == ANN_U8 ? OP_U8 : OP_F32, idx->dim, 1, nq, idx->dim, nullptr};
     st = launch_tower(m, X, nq, qhat, qbf, nullptr, nullptr, nullptr, idx->d_status, s);
-    if (st == ANN_OK && mode == ANN_ENTRY_LEARNED_EXHAUSTIVE) {
-        const Operand Q{qbf, OP_BF16, 64, 1, nq, 64, nullptr};
-        st = launch_hub_argmax(m, Q, nq, d_entry, hid, hsc, idx->d_status, s, m_seeds);
-    } else if (st == ANN_OK && L_hub <= kNavMaxPool && m->s <= 32) {
+    if (st == ANN_OK && L_hub <= kNavMaxPool && m->s <= 32) {
         // the hub-graph search in one launch (pools of up to 64 hubs)
         const int bm_words = (m->H + 127) / 128 * 4;
         const size_t per_warp = 256 + 4 * static_cast<size_t>(bm_words);

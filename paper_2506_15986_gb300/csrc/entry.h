@@ -34,6 +34,11 @@ ann_status build_hub_index(ann_index *idx, ann_entry_model *m, const int32_t *hu
 ann_status launch_tower(const ann_entry_model *m, const Operand &X, int64_t nq, float *qhat,
                         __nv_bfloat16 *qhat_bf, float *z1, __nv_bfloat16 *a1, float *nrm, int *status,
                         cudaStream_t s);
+// Exhaustive entry selection in one kernel: the query tower, every hub's
+// score and the topm (1..8) best hubs' nodes per query (nq x topm, best
+// first); qhat (optional) receives the fp32 query embeddings.
+ann_status launch_entry_exhaustive(const ann_entry_model *m, const Operand &X, int64_t nq, float *qhat,
+                                   int32_t *out_node, int topm, int *status, cudaStream_t s);
 // Exhaustive hub scoring: the topm (1..8) best hubs per query, nq x topm
 // outputs, best first.
 ann_status launch_hub_argmax(const ann_entry_model *m, const Operand &Q, int64_t nq, int32_t *out_node,

@@ -237,22 +237,6 @@ ann_status ann_autotune(ann_index *idx, const void *d_queries, int64_t nq, const
             }
         }
     }
-    // stage 5: first-level visited tables kept resident in L2 (applied by
-    // the launch only when they fit the persisting-L2 capacity), at the best
-    // table size so far and one and two sizes smaller (smaller tables fit
-    // more often; their longer probe chains then hit in L2)
-    {
-        const ann_search_params b4 = bp;
-        const int sbb = b4.spill_bits > 0 ? b4.spill_bits : ann::default_spill_bits(p->L);
-        for (int sb = sbb; ok && sb >= sbb - 2; --sb) {
-            if (sb < 10 || sb > 16)
-                continue;
-            ann_search_params c = b4;
-            c.flags |= ANN_SEARCH_VISITED_L2;
-            c.spill_bits = sb;
-            ok = trial(c);
-        }
-    }
     // the caller's outputs hold the chosen combination's results
     if (ok && bms < 1e30f)
         st = ann_search_batch(idx, d_queries, nq, d_entry, &bp, d_ids, d_dists, nullptr, s);

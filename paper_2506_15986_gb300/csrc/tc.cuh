@@ -160,10 +160,29 @@ __device__ __forceinline__ uint4 op_load8(const Operand &o, int64_t r, int64_t k
 }
 
 // Stage rows [r0, r0+ROWS) x k [k0, k0+8*KG) of `o` into a canonical tile.
+// In a 128-thread CTA each thread takes chunks threadIdx.x, +128, ... and
+// loads up to four of them before storing any, so their global loads are in
+// flight together instead of one after another.
 template <int ROWS, int KG>
 __device__ __forceinline__ void stage_tile(uint8_t *tile, const Operand &o, int64_t r0, int64_t k0)
 {
     constexpr int CHUNKS = ROWS * KG;
+    if (CHUNKS % 128 == 0 && blockDim.x == 128) {
+        constexpr int PER = CHUNKS / 128;
+        constexpr int NB = PER < 4 ? PER : 4;
+        for (int b0 = 0; b0 < PER; b0 += NB) {
+            uint4 v[NB];
+#pragma unroll
+            for (int i = 0; i < NB; ++i) {
+                const int c = (b0 + i) * 128 + static_cast<int>(threadIdx.x);
+                v[i] = op_load8(o, r0 + (c / (8 * KG)) * 8 + (c & 7), k0 + ((c >> 3) % KG) * 8);
+            }
+#pragma unroll
+            for (int i = 0; i < NB; ++i)
+                *reinterpret_cast<uint4 *>(tile + ((b0 + i) * 128 + threadIdx.x) * 16) = v[i];
+        }
+        return;
+    }
     for (int c = threadIdx.x; c < CHUNKS; c += blockDim.x) {
         const int r = (c / (8 * KG)) * 8 + (c & 7);
         const int kg = (c >> 3) % KG;

@@ -216,7 +216,7 @@ def test_empty_batch_and_bad_device_inputs(c1):
     assert ann.ann_sync_status(c1["h"]) == ann.OK  # cleared by the read
     # host-side parameter checks return before any launch
     for kw in (dict(team=3), dict(team=64), dict(stage_rows=33), dict(W=5), dict(hash_bits=7), dict(hash_bits=-2),
-               dict(spill_bits=9), dict(spill_bits=17), dict(flags=4),
+               dict(spill_bits=9), dict(spill_bits=17), dict(flags=8), dict(gather=2),
                dict(entries=np.zeros((4, 33), np.int32))):
         with pytest.raises(ann.AnnError) as e:
             search(c1["h"], q[:4], 10, 64, **kw)
