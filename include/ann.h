@@ -140,7 +140,10 @@ typedef struct {
  *             that hit in L2); otherwise it launches without one.  The first
  *             such call on a device outside stream capture raises the
  *             context's persisting-L2 limit (cudaLimitPersistingL2CacheSize)
- *             to the device maximum; the limit ends with the process.
+ *             to the device maximum; the limit ends with the process.  The
+ *             persisting lines outlive the call and keep their share of L2
+ *             from later kernels that do not use it (cudaCtxResetPersistingL2Cache
+ *             releases them), so use it in a process whose searches all do.
  *             ANN_SEARCH_FAULT_WAIT: fault injection for testing; every wait
  *             for a round of gathered rows gives up at once, as if its time
  *             limit had passed: each query fails with -1 ids and the call
@@ -273,6 +276,15 @@ ann_status ann_search_batch(ann_index *idx, const void *d_queries, int64_t nq,
  * The device status word of the Sec. 2.1 search (no paper passage).
  */
 ann_status ann_sync_status(ann_index *idx, void *stream);
+
+/*
+ * Returns the L2 lines that searches with ANN_SEARCH_VISITED_L2 left
+ * persisting on the index's device to normal status (every persisting line
+ * of this process's context on that device), so that later work without the
+ * flag gets the whole L2 back.  Waits for the device first.  A cache-residency
+ * control of this implementation (no paper passage); ANN_ERR_CUDA on failure.
+ */
+ann_status ann_release_l2(ann_index *idx);
 
 /* ---- batching line: CUDA-graph plans and the autotuner -------------------- */
 

@@ -109,6 +109,7 @@ def load_library(path: str | None = None):
         "ann_hub_costs": ([_p, _p, i64, _p, _p, i32, _p, i32, i32, _p, _p, _p], i32),
         "ann_hub_labels": ([_p, _p, _p, i64, i32, i32, i32, _p, _p, _p], i32),
         "ann_map_ids": ([_p, i64, _p, i64, _p, _p], i32),
+        "ann_release_l2": ([_p], i32),
         "ann_merge_shards": ([_p, _p, i32, i64, i32, i32, _p, _p, _p], i32),
     }
     for name, (args, res) in sig.items():
@@ -379,6 +380,11 @@ def ann_hub_labels(evals, hops, cand, nq, M, t_pos, t_neg, labels, best=None, st
     _check(load_library().ann_hub_labels(_ptr(evals), _ptr(hops), _ptr(cand), int(nq), int(M),
                                          int(t_pos), int(t_neg), _ptr(labels), _ptr(best), _stream(stream)),
            "ann_hub_labels")
+
+
+def ann_release_l2(h):
+    """Return persisting L2 lines of ANN_SEARCH_VISITED_L2 searches to normal (blocking)."""
+    _check(load_library().ann_release_l2(h), "ann_release_l2")
 
 
 def ann_map_ids(ids, count, id_map, n_map, status=None, stream=None):

@@ -457,6 +457,17 @@ ann_status ann_search_batch(ann_index *idx, const void *d_queries, int64_t nq, c
     return launch_search(idx, L, static_cast<cudaStream_t>(stream));
 }
 
+ann_status ann_release_l2(ann_index *idx)
+{
+    if (!idx)
+        return ANN_ERR_INVALID_ARG;
+    DeviceGuard guard(idx->device);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess)
+        e = cudaCtxResetPersistingL2Cache();
+    return e == cudaSuccess ? ANN_OK : ANN_ERR_CUDA;
+}
+
 ann_status ann_sync_status(ann_index *idx, void *stream)
 {
     if (!idx)

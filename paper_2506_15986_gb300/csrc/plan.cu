@@ -237,9 +237,35 @@ ann_status ann_autotune(ann_index *idx, const void *d_queries, int64_t nq, const
             }
         }
     }
-    // the caller's outputs hold the chosen combination's results
+    // stage 5: first-level visited tables kept resident in L2 (applied by
+    // the launch only when they fit the persisting-L2 capacity), at the best
+    // table size so far and one and two sizes smaller; the lines a trial
+    // leaves persisting are released before the next trial, so no other
+    // candidate is timed with a smaller L2
+    {
+        const ann_search_params b4 = bp;
+        const int sbb = b4.spill_bits > 0 ? b4.spill_bits : ann::default_spill_bits(p->L);
+        for (int sb = sbb; ok && sb >= sbb - 2; --sb) {
+            if (sb < 10 || sb > 16)
+                continue;
+            ann_search_params c = b4;
+            c.flags |= ANN_SEARCH_VISITED_L2;
+            c.spill_bits = sb;
+            ok = trial(c);
+            if (cudaDeviceSynchronize() != cudaSuccess || cudaCtxResetPersistingL2Cache() != cudaSuccess) {
+                st = ANN_ERR_CUDA;
+                ok = false;
+            }
+        }
+    }
+    // the caller's outputs hold the chosen combination's results; lines it
+    // leaves persisting are released (the caller's own searches with the
+    // chosen flags make them resident again)
     if (ok && bms < 1e30f)
         st = ann_search_batch(idx, d_queries, nq, d_entry, &bp, d_ids, d_dists, nullptr, s);
+    if (st == ANN_OK && (bp.flags & ANN_SEARCH_VISITED_L2) &&
+        (cudaDeviceSynchronize() != cudaSuccess || cudaCtxResetPersistingL2Cache() != cudaSuccess))
+        st = ANN_ERR_CUDA;
     for (int i = 1; i < lanes; ++i)
         if (ls[i] != s) {
             cudaStreamSynchronize(ls[i]);

@@ -113,3 +113,7 @@ def test_index_header_limits_checked_before_allocating(lib, tmp_path):
         p = tmp_path / f"hdr_{dim}_{degree}.idx"
         p.write_bytes(hdr)
         assert lib.ann_load_index(str(p).encode(), 0, ctypes.byref(out)) == ann.ERR_FORMAT
+
+
+def test_release_l2_needs_an_index(lib):
+    assert lib.ann_release_l2(None) == ann.ERR_INVALID_ARG

@@ -102,7 +102,8 @@ def test_autotune_keeps_results(case, lanes):
     ref = ids.clone(), dd.clone()
     ids.fill_(-7)
     best, ms = ann.ann_autotune(case["h"], q, nq, None, p, ids, dd, reps=3, lanes=lanes)
-    assert ms > 0 and (best.hash_bits >= 8 or best.hash_bits == -1) and best.stage_rows in (4, 8, 12, 16)
+    assert ms > 0 and (best.hash_bits >= 8 or best.hash_bits == -1) and best.stage_rows in (4, 6, 8, 12, 16)
+    assert best.gather in (0, 4) and best.flags & ~ann.SEARCH_VISITED_L2 == 0
     assert best.team in (2, 4, 8, 16, 32) and best.spill_bits in (0, 10, 11, 12, 13, 14, 15, 16)
     tuned = ids.clone(), dd.clone()  # the autotuner leaves the chosen combination's results
     ann.ann_search_batch(case["h"], q, nq, None, best, ids, dd)

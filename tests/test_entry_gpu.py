@@ -173,6 +173,29 @@ def test_nav_search_matches_oracle(setup, L_hub):
     assert S[r, oi[:, 0]].mean() - S[r, chosen].mean() <= 1e-4
 
 
+def test_nav_with_hubs_beyond_shared_memory_matches_oracle(setup):
+    # 2,048 hubs (their rows and graph do not fit one CTA's shared memory):
+    # the hub-graph search reads them through L2, against the oracle's walk
+    H = 2048
+    W1, b1, W2, b2, _ = setup["W"]
+    E = np.random.default_rng(5).standard_normal((H, 64)).astype(np.float32)
+    hub_nodes = np.random.default_rng(6).choice(6000, H, replace=False).astype(np.int32)
+    adj, ent = oracle.hub_graph(E.astype(np.float64), 16)
+    h = ann.ann_index_create(setup["base"], setup["graph"], setup["medoid"], ann.F32, ann.L2)
+    try:
+        ann.ann_set_entry_model(h, 128, W1, b1, W2, b2, hub_nodes, E, 16, hub_graph=adj, hub_entry=ent)
+        s = dict(setup, h=h)
+        for L_hub in (16, 40):
+            got, _ = _select(s, ann.ENTRY_LEARNED_NAV, L_hub=L_hub)
+            # distinct hub nodes: the chosen node names the chosen hub
+            Eb = _eb(E).astype(np.float32)
+            ref_q = _oracle_qhat(setup["q"], setup["W"])
+            oi, _, _, _ = oracle.search(Eb, adj, ref_q, ent, L_hub, 1, metric=oracle.IP)
+            assert (got == hub_nodes[oi[:, 0]]).mean() >= 0.99
+    finally:
+        ann.ann_free_index(h)
+
+
 def test_nav_with_full_pool_equals_exhaustive(setup):
     # special case: a pool as large as the hub set evaluates every hub
     # reachable from the entry hub, so the greedy search returns the
