@@ -139,11 +139,10 @@ typedef struct {
  *             keeps them resident in L2 (no write-back, and compare-and-swaps
  *             that hit in L2); otherwise it launches without one.  The first
  *             such call on a device outside stream capture raises the
- *             context's persisting-L2 limit (cudaLimitPersistingL2CacheSize)
- *             to the device maximum; the limit ends with the process.  The
- *             persisting lines outlive the call and keep their share of L2
- *             from later kernels that do not use it (cudaCtxResetPersistingL2Cache
- *             releases them), so use it in a process whose searches all do.
+ *             context's persisting-L2 set-aside (cudaLimitPersistingL2CacheSize)
+ *             to the device maximum.  While the set-aside is raised, accesses
+ *             without a persisting window use only the rest of L2, and the
+ *             persisting lines outlive the call: ann_release_l2 undoes both.
  *             ANN_SEARCH_FAULT_WAIT: fault injection for testing; every wait
  *             for a round of gathered rows gives up at once, as if its time
  *             limit had passed: each query fails with -1 ids and the call
@@ -278,10 +277,12 @@ ann_status ann_search_batch(ann_index *idx, const void *d_queries, int64_t nq,
 ann_status ann_sync_status(ann_index *idx, void *stream);
 
 /*
- * Returns the L2 lines that searches with ANN_SEARCH_VISITED_L2 left
- * persisting on the index's device to normal status (every persisting line
- * of this process's context on that device), so that later work without the
- * flag gets the whole L2 back.  Waits for the device first.  A cache-residency
+ * Undoes what searches with ANN_SEARCH_VISITED_L2 left in the L2 of the
+ * index's device: every persisting line of this process's context there
+ * returns to normal status and the context's persisting-L2 set-aside
+ * (cudaLimitPersistingL2CacheSize) returns to zero, so that later work
+ * without the flag has the whole L2 again (the next flagged search raises
+ * the set-aside again).  Waits for the device first.  A cache-residency
  * control of this implementation (no paper passage); ANN_ERR_CUDA on failure.
  */
 ann_status ann_release_l2(ann_index *idx);

@@ -462,9 +462,13 @@ ann_status ann_release_l2(ann_index *idx)
     if (!idx)
         return ANN_ERR_INVALID_ARG;
     DeviceGuard guard(idx->device);
+    // the lines back to normal, and the set-aside back to zero: while it is
+    // above zero, accesses without a persisting window use only the rest of L2
     cudaError_t e = cudaDeviceSynchronize();
     if (e == cudaSuccess)
         e = cudaCtxResetPersistingL2Cache();
+    if (e == cudaSuccess)
+        e = cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, 0);
     return e == cudaSuccess ? ANN_OK : ANN_ERR_CUDA;
 }
 

@@ -565,16 +565,9 @@ __global__ void map_hub_seeds(const int32_t *hub_ids, int64_t nq, int m, const i
 // L smallest keys of every hub evaluated, a hub is evaluated once, the search
 // stops when no unexpanded entry is left.  The m best pool entries become the
 // seeds (their hubs' nodes).
-// With the hub rows and the hub graph in shared memory (they fit for about
-// a thousand hubs), one persistent CTA of kNavWarpsSmem warps per SM loads
-// them once and walks every step from shared memory; otherwise CTAs of
-// kNavWarps warps read them through L2.
 constexpr int kNavWarps = 8;
-constexpr int kNavWarpsSmem = 32;
 constexpr int kNavMaxPool = 64;
 
-// G: the hub row is in global memory (read through the read-only path)
-template <bool G>
 __device__ __forceinline__ float hub_score(const float *q, const __nv_bfloat16 *row)
 {
     // -<q, e> with four FP32 accumulators over coordinates j mod 4
@@ -583,7 +576,7 @@ __device__ __forceinline__ float hub_score(const float *q, const __nv_bfloat16 *
     float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
 #pragma unroll 4
     for (int c = 0; c < 8; ++c) {
-        const uint4 x = G ? __ldg(r4 + c) : r4[c];
+        const uint4 x = __ldg(r4 + c);
         const float4 qa = q4[2 * c], qb = q4[2 * c + 1];
         const float2 f0 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&x.x));
         const float2 f1 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&x.y));
@@ -620,38 +613,20 @@ __device__ __forceinline__ void merge32(uint64_t a, uint64_t b, int lane, uint64
 }
 
 // NP keys per lane: pools of up to 32 * NP hubs (element r * 32 + lane in
-// pool[r]).  NW warps per CTA; SMT: the hub rows and the hub graph are first
-// copied into shared memory (tab_bytes of it, before the per-warp regions),
-// the rows kNavRowSmem bytes apart: 144 = 128 + 16, so that the lanes'
-// 16-byte reads of the same chunk of different rows fall on different banks.
-constexpr int kNavRowSmem = 144;
-template <int NP, int NW, bool SMT>
-__global__ void __launch_bounds__(32 * NW, NW >= 32 ? 1 : 4)
-    hub_nav_kernel(const float *qhat, int64_t nq, const __nv_bfloat16 *Eb_g, int H, const int32_t *hgraph_g, int s,
+// pool[r]).
+template <int NP>
+__global__ void __launch_bounds__(32 * kNavWarps, 4)
+    hub_nav_kernel(const float *qhat, int64_t nq, const __nv_bfloat16 *Eb, int H, const int32_t *hgraph, int s,
                    int32_t entry, int L, int m_seeds, const int32_t *hub_nodes, int32_t medoid, int bm_words,
-                   int tab_bytes, int32_t *out)
+                   int32_t *out)
 {
     extern __shared__ __align__(16) uint8_t nav_smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const __nv_bfloat16 *Eb = Eb_g;
-    const int32_t *hgraph = hgraph_g;
-    if constexpr (SMT) {
-        for (int i = threadIdx.x; i < H * 8; i += blockDim.x)
-            *reinterpret_cast<uint4 *>(nav_smem + (i >> 3) * kNavRowSmem + (i & 7) * 16) =
-                reinterpret_cast<const uint4 *>(Eb_g)[i];
-        int32_t *g = reinterpret_cast<int32_t *>(nav_smem + static_cast<size_t>(H) * kNavRowSmem);
-        for (int i = threadIdx.x; i < H * s; i += blockDim.x)
-            g[i] = hgraph_g[i];
-        __syncthreads();
-        Eb = reinterpret_cast<const __nv_bfloat16 *>(nav_smem);
-        hgraph = g;
-    }
-    const int row_elems = SMT ? kNavRowSmem / 2 : 64;  // BF16 elements from one hub row to the next
     const int per_warp = 256 + 4 * bm_words;
-    float *q = reinterpret_cast<float *>(nav_smem + tab_bytes + wid * per_warp);
-    uint32_t *vis = reinterpret_cast<uint32_t *>(nav_smem + tab_bytes + wid * per_warp + 256);
-    for (int64_t qi = blockIdx.x * static_cast<int64_t>(NW) + wid; qi < nq;
-         qi += static_cast<int64_t>(gridDim.x) * NW) {
+    float *q = reinterpret_cast<float *>(nav_smem + wid * per_warp);
+    uint32_t *vis = reinterpret_cast<uint32_t *>(nav_smem + wid * per_warp + 256);
+    for (int64_t qi = blockIdx.x * static_cast<int64_t>(kNavWarps) + wid; qi < nq;
+         qi += static_cast<int64_t>(gridDim.x) * kNavWarps) {
         if (lane < 16)
             reinterpret_cast<float4 *>(q)[lane] = reinterpret_cast<const float4 *>(qhat + qi * 64)[lane];
         for (int w = lane; w < bm_words; w += 32)
@@ -664,7 +639,7 @@ __global__ void __launch_bounds__(32 * NW, NW >= 32 ? 1 : 4)
             pool[r] = kKeyMax;
         if (lane == 0) {
             vis[entry >> 5] = 1u << (entry & 31);
-            pool[0] = make_key(f32_to_ord(hub_score<!SMT>(q, Eb + static_cast<int64_t>(entry) * row_elems)), entry);
+            pool[0] = make_key(f32_to_ord(hub_score(q, Eb + static_cast<int64_t>(entry) * 64)), entry);
         }
         for (;;) {
             // the first unexpanded entry in pool order
@@ -690,14 +665,12 @@ __global__ void __launch_bounds__(32 * NW, NW >= 32 ? 1 : 4)
                     node = v;
             }
             __syncwarp();
-            const int32_t nb = lane < s ? (SMT ? hgraph[static_cast<int64_t>(node) * s + lane]
-                                               : __ldg(hgraph + static_cast<int64_t>(node) * s + lane))
-                                        : -1;
+            const int32_t nb = lane < s ? __ldg(hgraph + static_cast<int64_t>(node) * s + lane) : -1;
             uint64_t cand = kKeyMax;
             if (nb >= 0 && nb < H) {
                 const uint32_t bit = 1u << (nb & 31);
                 if (!(atomicOr(&vis[nb >> 5], bit) & bit))
-                    cand = make_key(f32_to_ord(hub_score<!SMT>(q, Eb + static_cast<int64_t>(nb) * row_elems)), nb);
+                    cand = make_key(f32_to_ord(hub_score(q, Eb + static_cast<int64_t>(nb) * 64)), nb);
             }
             cand = warp_sort32(cand, lane);
             // the pool keeps the L smallest keys of itself and the new ones:
@@ -1089,24 +1062,16 @@ ann_status ann_select_entries(ann_index *idx, const void *d_queries, int64_t nq,
         // the hub-graph search in one launch (pools of up to 64 hubs)
         const int bm_words = (m->H + 127) / 128 * 4;
         const size_t per_warp = 256 + 4 * static_cast<size_t>(bm_words);
-        const size_t tab =
-            (static_cast<size_t>(m->H) * kNavRowSmem + static_cast<size_t>(m->H) * m->s * 4 + 15) / 16 * 16;
-        int max_smem = 0;
-        cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, idx->device);
-        const bool smt = tab + per_warp * kNavWarpsSmem <= static_cast<size_t>(max_smem);
-        const size_t smem = smt ? tab + per_warp * kNavWarpsSmem : per_warp * kNavWarps;
-        const int nw = smt ? kNavWarpsSmem : kNavWarps;
-        auto kern = smt ? (L_hub <= 32 ? hub_nav_kernel<1, kNavWarpsSmem, true> : hub_nav_kernel<2, kNavWarpsSmem, true>)
-                        : (L_hub <= 32 ? hub_nav_kernel<1, kNavWarps, false> : hub_nav_kernel<2, kNavWarps, false>);
+        const size_t smem = per_warp * kNavWarps;
+        auto kern = L_hub <= 32 ? hub_nav_kernel<1> : hub_nav_kernel<2>;
         cudaError_t e =
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
         if (e == cudaSuccess) {
-            // tables in shared memory: one persistent CTA per SM (each loads them once)
-            const int64_t cap = static_cast<int64_t>(idx->num_sms) * (smt ? 1 : 8);
-            const int64_t blocks = std::min<int64_t>((nq + nw - 1) / nw, cap);
-            kern<<<static_cast<unsigned>(blocks), 32 * nw, smem, s>>>(
+            const int64_t blocks = std::min<int64_t>((nq + kNavWarps - 1) / kNavWarps,
+                                                     static_cast<int64_t>(idx->num_sms) * 8);
+            kern<<<static_cast<unsigned>(blocks), 32 * kNavWarps, smem, s>>>(
                 qhat, nq, m->Eb, m->H, m->hub_graph, m->s, m->hub_entry, L_hub, m_seeds, m->hub_nodes, idx->medoid,
-                bm_words, smt ? static_cast<int>(tab) : 0, d_entry);
+                bm_words, d_entry);
             e = cudaGetLastError();
         }
         st = cuda_status(e);

@@ -252,7 +252,7 @@ ann_status ann_autotune(ann_index *idx, const void *d_queries, int64_t nq, const
             c.flags |= ANN_SEARCH_VISITED_L2;
             c.spill_bits = sb;
             ok = trial(c);
-            if (cudaDeviceSynchronize() != cudaSuccess || cudaCtxResetPersistingL2Cache() != cudaSuccess) {
+            if (ann_release_l2(idx) != ANN_OK) {
                 st = ANN_ERR_CUDA;
                 ok = false;
             }
@@ -263,9 +263,8 @@ ann_status ann_autotune(ann_index *idx, const void *d_queries, int64_t nq, const
     // chosen flags make them resident again)
     if (ok && bms < 1e30f)
         st = ann_search_batch(idx, d_queries, nq, d_entry, &bp, d_ids, d_dists, nullptr, s);
-    if (st == ANN_OK && (bp.flags & ANN_SEARCH_VISITED_L2) &&
-        (cudaDeviceSynchronize() != cudaSuccess || cudaCtxResetPersistingL2Cache() != cudaSuccess))
-        st = ANN_ERR_CUDA;
+    if (st == ANN_OK && (bp.flags & ANN_SEARCH_VISITED_L2))
+        st = ann_release_l2(idx);
     for (int i = 1; i < lanes; ++i)
         if (ls[i] != s) {
             cudaStreamSynchronize(ls[i]);

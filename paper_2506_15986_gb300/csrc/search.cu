@@ -29,7 +29,6 @@
 #include <stdint.h>
 
 #include <algorithm>
-#include <atomic>
 
 #include "device_util.cuh"
 #include "internal.h"
@@ -903,26 +902,21 @@ ann_status launch_typed(const SearchArgs &a, size_t smem, int teams, int wpc, cu
 
 // Bytes of L2 the first-level visited tables may keep resident on the
 // current device: the device's persisting-L2 maximum, to which the context's
-// limit is raised once (outside stream capture) for ANN_SEARCH_VISITED_L2.
+// set-aside is raised (outside stream capture) when it is lower, for
+// ANN_SEARCH_VISITED_L2; ann_release_l2 lowers it again.
 size_t persisting_l2_bytes(int dev, cudaStream_t s)
 {
-    constexpr int kMaxDevices = 64;
-    static std::atomic<int> raised[kMaxDevices];
-    if (dev < 0 || dev >= kMaxDevices)
-        return 0;
     int maxp = 0;
     if (cudaDeviceGetAttribute(&maxp, cudaDevAttrMaxPersistingL2CacheSize, dev) != cudaSuccess || maxp <= 0)
         return 0;
     size_t cur = 0;
     if (cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize) != cudaSuccess)
         return 0;
-    if (cur < static_cast<size_t>(maxp) && !raised[dev].load()) {
+    if (cur < static_cast<size_t>(maxp)) {
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
         if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone &&
-            cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, static_cast<size_t>(maxp)) == cudaSuccess) {
-            raised[dev].store(1);
+            cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, static_cast<size_t>(maxp)) == cudaSuccess)
             cur = static_cast<size_t>(maxp);
-        }
         cudaGetLastError();
     }
     return cur;

@@ -173,9 +173,9 @@ def test_nav_search_matches_oracle(setup, L_hub):
     assert S[r, oi[:, 0]].mean() - S[r, chosen].mean() <= 1e-4
 
 
-def test_nav_with_hubs_beyond_shared_memory_matches_oracle(setup):
-    # 2,048 hubs (their rows and graph do not fit one CTA's shared memory):
-    # the hub-graph search reads them through L2, against the oracle's walk
+def test_nav_with_two_thousand_hubs_matches_oracle(setup):
+    # a hub set seven times larger (a wider visited bitmap per warp), two
+    # pool sizes, against the oracle's walk
     H = 2048
     W1, b1, W2, b2, _ = setup["W"]
     E = np.random.default_rng(5).standard_normal((H, 64)).astype(np.float32)
