@@ -129,7 +129,7 @@ MEASURED_TRAFFIC = {
     # algorithmic bytes to the headline launch (5.167 GB).
     "shift": [
         dict(digest="12c2cd3eb4cfce87", entry="exhaustive", L=93, nq=10_000, hash_bits=-1, stage_rows=8,
-             team=4, spill_bits=0, gather=0, visited_l2=False,
+             team=4, spill_bits=0, gather=0, visited_l2=False, group_entries=False,
              bytes=(4.544243e9 + 0.806115e9) * 5.167231e9 / 6.215410e9),
     ],
 }
@@ -192,7 +192,7 @@ def parse():
     ap.add_argument("--fixed-L", type=int, default=0,
                     help="skip the L sweep and run every entry mode at this pool size")
     ap.add_argument("--knobs", default="",
-                    help="fixed search sizes hash_bits,stage_rows,team,spill_bits,gather[,visited_l2] instead of "
+                    help="fixed search sizes hash_bits,stage_rows,team,spill_bits,gather[,visited_l2[,group_entries]] instead of "
                          "ann_autotune (for a profiler capture of one known configuration)")
     ap.add_argument("--alpha", type=float, default=1.0,
                     help="RNG pruning factor of the graph builder (c is dropped when a kept s has "
@@ -572,6 +572,7 @@ class Runner:
         return {"hash_bits": best.hash_bits, "stage_rows": best.stage_rows, "team": best.team,
                 "spill_bits": best.spill_bits, "gather": best.gather,
                 "visited_l2": bool(best.flags & self.ann.SEARCH_VISITED_L2),
+                "group_entries": bool(best.flags & self.ann.SEARCH_GROUP_ENTRIES),
                 "search_ms": ms}
 
     def select(self, q):
@@ -801,14 +802,16 @@ def measure_mode(run, torch, ann, W, args, targets):
     else:
         Lstar, sw, per = sweep(run, torch, ann, W, targets)
     if args.knobs:
-        hb, sr, tm, sb, ga, vl = (int(x) for x in (args.knobs + ",0").split(",")[:6])
+        hb, sr, tm, sb, ga, vl, gr = (int(x) for x in (args.knobs + ",0,0").split(",")[:7])
         p = run.params(Lstar)
         p.hash_bits, p.stage_rows, p.team, p.spill_bits, p.gather = hb, sr, tm, sb, ga
         if vl:
             p.flags |= ann.SEARCH_VISITED_L2
+        if gr:
+            p.flags |= ann.SEARCH_GROUP_ENTRIES
         run.tuned[Lstar] = p
         tune = {"hash_bits": hb, "stage_rows": sr, "team": tm, "spill_bits": sb, "gather": ga,
-                "visited_l2": bool(vl), "fixed": True}
+                "visited_l2": bool(vl), "group_entries": bool(gr), "fixed": True}
     else:
         tune = None if args.no_tune else run.autotune(Lstar)
     run.step(Lstar, stats=True)
@@ -973,7 +976,8 @@ def batch_report(W, torch, ann, args, dev, modes):
             "evals_per_query": float(s[:, 0].mean()), "hops_per_query": float(s[:, 1].mean()),
             "tuned": {"hash_bits": best.hash_bits, "stage_rows": best.stage_rows, "team": best.team,
                       "spill_bits": best.spill_bits, "gather": best.gather,
-                      "visited_l2": bool(best.flags & ann.SEARCH_VISITED_L2)},
+                      "visited_l2": bool(best.flags & ann.SEARCH_VISITED_L2),
+                      "group_entries": bool(best.flags & ann.SEARCH_GROUP_ENTRIES)},
             "batch": B, "batch_latency_ms": {"p50": float(np.percentile(lat, 50)),
                                              "p99": float(np.percentile(lat, 99))},
             "plan_latency_ms": {"p50": float(np.percentile(lat_plan, 50)),
@@ -1052,7 +1056,8 @@ def run_gpu(args):
         if mt["digest"] == kernel_digest() and mt["entry"] == head and mt["L"] == R["L"] \
                 and mt["nq"] == R["run"].nq \
                 and all(tn.get(key) == mt[key]
-                        for key in ("hash_bits", "stage_rows", "team", "spill_bits", "gather", "visited_l2")):
+                        for key in ("hash_bits", "stage_rows", "team", "spill_bits", "gather", "visited_l2",
+                                    "group_entries")):
             traffic = mt["bytes"]
     out = None
     if rank == 0:

@@ -61,6 +61,7 @@ typedef struct ann_index ann_index;
 #define ANN_SEARCH_RERANK 1u /* re-score the final pool from the fp32 copy (see ann_index_desc.base_f32) */
 #define ANN_SEARCH_FAULT_WAIT 2u /* fault injection for tests of the timeout path (see ann_search_params) */
 #define ANN_SEARCH_VISITED_L2 4u /* keep the first-level visited tables resident in L2 (see ann_search_params) */
+#define ANN_SEARCH_GROUP_ENTRIES 8u /* run queries grouped by their first seed (see ann_search_params) */
 
 /* Limits of one search */
 #define ANN_MAX_L 4096     /* pool size L */
@@ -143,7 +144,15 @@ typedef struct {
  *             to the device maximum.  While the set-aside is raised, accesses
  *             without a persisting window use only the rest of L2, and the
  *             persisting lines outlive the call: ann_release_l2 undoes both.
- *             ANN_SEARCH_FAULT_WAIT: fault injection for testing; every wait
+ *             ANN_SEARCH_GROUP_ENTRIES (speed only): with entries given, the
+             launch first sorts the work items by a hash of their first seed
+             (one extra single-CTA kernel, 4 bytes of scratch per item) and
+             the persistent teams take them in that order, so queries that
+             start at the same node run side by side and share the rows of
+             their first steps in L2.  Every item's outputs are written at its
+             own index and do not depend on the order.  Ignored with the
+             medoid entry (d_entry NULL).
+             ANN_SEARCH_FAULT_WAIT: fault injection for testing; every wait
  *             for a round of gathered rows gives up at once, as if its time
  *             limit had passed: each query fails with -1 ids and the call
  *             reports ANN_ERR_TIMEOUT through ann_sync_status.  The copies in
@@ -202,8 +211,8 @@ int32_t ann_i8s_row_bytes(int32_t dim);
  * 127; code_j = x_j / scale rounded half to even and clipped to [-127, 127];
  * an all-zero row gets scale 0 and zero codes.  dim must be a multiple of 4.
  * Asynchronous on stream.
- * The int8-with-scale storage of the precision line (a spec choice;
- * the paper fixes no precision).
+ * The int8-with-scale storage of the precision line (a storage choice of this
+ * library; the paper fixes no precision).
  */
 ann_status ann_quantize_i8s(const float *d_x, int64_t n, int32_t dim, void *d_rows, void *stream);
 
@@ -308,7 +317,7 @@ ann_status ann_plan_create(ann_index *idx, const void *d_queries, int64_t nq, in
 
 /*
  * Launch a captured batch on `stream` (asynchronous).
- * The batching line (the benchmark spec): one captured batch of Sec. 4.3 entry
+ * The batched serving path: one captured batch of Sec. 4.3 entry
  * selection and Sec. 2.1 search. ANN_ERR_INVALID_ARG for a NULL plan.
  */
 ann_status ann_plan_launch(ann_plan *plan, void *stream);
@@ -320,13 +329,20 @@ ann_status ann_plan_launch(ann_plan *plan, void *stream);
 ann_status ann_plan_free(ann_plan *plan);
 
 /*
- * Time ann_search_batch over the given batch for visited-table sizes around
- * and below the default and no shared table (hash_bits), gather round sizes
- * (stage_rows 4, 8, 12, 16),
- * distance team sizes (team 2 to 32 where a lane gets 1 to 16 16-byte chunks
- * of the row) and first spill-table sizes (spill_bits up to two either side
- * of the default), one after the other, and return in *best the copy of *p
- * with the fastest combination (*best_ms: its time per batch).
+ * Time ann_search_batch over the given batch for a sequence of speed knobs,
+ * each stage starting from the fastest combination so far, and return in
+ * *best the copy of *p with the fastest combination (*best_ms: its time per
+ * batch).  The stages:
+ *   1. hash_bits (no shared table, and sizes around and below the default)
+ *      x stage_rows 4, 6, 8, 12, 16;
+ *   2. team 2 to 32, where a lane gets 1 to 16 16-byte chunks of the row;
+ *   3. spill_bits up to two either side of the default;
+ *   4. gather 4 (when the index's rows allow TMA tensor gathers) with
+ *      stage_rows 8, 12, 16 and team the best or 8;
+ *   5. ANN_SEARCH_VISITED_L2 with spill_bits the best and one and two less
+ *      (ann_release_l2 after each such trial, and at the end when the chosen
+ *      combination has the flag);
+ *   6. ANN_SEARCH_GROUP_ENTRIES, when d_entry is given.
  *   reps   timed batches per combination, after one warm-up batch per lane
  *   lanes  1..8 streams the timed batches alternate over (batch r on lane
  *          r mod lanes), so that combinations are timed with consecutive
@@ -334,13 +350,12 @@ ann_status ann_plan_free(ann_plan *plan);
  *          that many streams; lane 0 is `stream`, the others are created and
  *          destroyed here and write to output buffers from the index's pool
  *   d_ids, d_dists  out: the results of the chosen combination
- * The visited set stays exact (shared table plus global spill) and the gather
- * order does not enter any result; the team size only moves float distances
- * by FP32 rounding.  Blocking.  Errors: ANN_ERR_INVALID_ARG for a NULL index,
- * params or best, nq < 1, reps < 1 or lanes outside 1..8; a search error
- * stops the tuning and is returned.
- * The batching line's autotuner (the benchmark spec); speed knobs of the Sec. 2.1
- * search only.
+ * The visited set stays exact (shared table plus global spill), and neither
+ * the gather mode nor the work order enters any result; the team size only
+ * moves float distances by FP32 rounding.  Blocking.  Errors:
+ * ANN_ERR_INVALID_ARG for a NULL index, params or best, nq < 1, reps < 1 or
+ * lanes outside 1..8; a search error stops the tuning and is returned.
+ * Speed knobs of the Sec. 2.1 search only (the batched serving path).
  */
 ann_status ann_autotune(ann_index *idx, const void *d_queries, int64_t nq, const int32_t *d_entry,
                         const ann_search_params *p, int32_t *d_ids, void *d_dists, int32_t reps,

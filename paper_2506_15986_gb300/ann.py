@@ -19,7 +19,7 @@ OK, ERR_INVALID_ARG, ERR_IO, ERR_FORMAT, ERR_OOM, ERR_CUDA, ERR_CAPACITY, ERR_TI
 # ann_dtype / ann_metric
 U8, F32, F16, BF16, I8S = 0, 1, 2, 3, 4
 L2, IP = 0, 1
-SEARCH_RERANK, SEARCH_FAULT_WAIT, SEARCH_VISITED_L2 = 1, 2, 4
+SEARCH_RERANK, SEARCH_FAULT_WAIT, SEARCH_VISITED_L2, SEARCH_GROUP_ENTRIES = 1, 2, 4, 8
 MAX_L, MAX_W, MAX_STEP_CAND, MAX_SEEDS, MAX_ENTRY_HUBS = 4096, 4, 128, 32, 8
 
 _c = ctypes

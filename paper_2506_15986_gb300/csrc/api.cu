@@ -432,7 +432,7 @@ ann_status ann_search_batch(ann_index *idx, const void *d_queries, int64_t nq, c
         (p->gather != 0 && p->gather != 1 && p->gather != 4) || p->n_entries < 0 ||
         p->n_entries > ANN_MAX_SEEDS || (p->n_entries > 1 && !d_entry))
         return ANN_ERR_INVALID_ARG;
-    if (p->flags & ~(ANN_SEARCH_RERANK | ANN_SEARCH_FAULT_WAIT | ANN_SEARCH_VISITED_L2))
+    if (p->flags & ~(ANN_SEARCH_RERANK | ANN_SEARCH_FAULT_WAIT | ANN_SEARCH_VISITED_L2 | ANN_SEARCH_GROUP_ENTRIES))
         return ANN_ERR_INVALID_ARG;
     if ((p->flags & ANN_SEARCH_RERANK) && !idx->d_base_f32)
         return ANN_ERR_UNSUPPORTED;  // the exact rerank needs the fp32 copy of the rows

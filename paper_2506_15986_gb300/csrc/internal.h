@@ -78,8 +78,9 @@ int default_team(int rowbytes);
 // spill_bits is 0: 40 evaluations per pool slot below 3/4 load, 12..15.
 int default_spill_bits(int L);
 
-// Scratch bytes launch_search needs for `teams` teams at the given params.
-size_t search_scratch_bytes(int teams, int spill_bits);
+// Scratch bytes launch_search needs for `teams` teams at the given params
+// (order_items: work items of a grouped work order, 0 without one).
+size_t search_scratch_bytes(int teams, int spill_bits, int64_t order_items);
 
 // Exact k-NN (build.cu): candidates from an fp32 GEMM, exact re-scoring.
 ann_status knn_exact(const void *d_base, int64_t n, int dim, int dtype, int metric, const void *d_queries,

@@ -258,6 +258,17 @@ ann_status ann_autotune(ann_index *idx, const void *d_queries, int64_t nq, const
             }
         }
     }
+    // stage 6: with entries given, the work order grouped by first seed at
+    // the best so far
+    if (ok && d_entry) {
+        ann_search_params c = bp;
+        c.flags |= ANN_SEARCH_GROUP_ENTRIES;
+        ok = trial(c);
+        if ((c.flags & ANN_SEARCH_VISITED_L2) && ann_release_l2(idx) != ANN_OK) {
+            st = ANN_ERR_CUDA;
+            ok = false;
+        }
+    }
     // the caller's outputs hold the chosen combination's results; lines it
     // leaves persisting are released (the caller's own searches with the
     // chosen flags make them resident again)

@@ -156,6 +156,50 @@ def test_visited_tables_kept_in_l2_change_nothing(c1, spill_bits):
     assert np.array_equal(d, od.astype(np.int64).astype(np.int32))
 
 
+@pytest.mark.parametrize("nq,m,n_hubs", [(20_000, 1, 8), (6_000, 4, 1_500), (1, 1, 1), (5_000, 1, 5_000)])
+def test_grouped_work_order_changes_nothing(c1, nq, m, n_hubs):
+    # ANN_SEARCH_GROUP_ENTRIES only changes the order in which the teams take
+    # the work items (sorted by a hash of the first seed): every item's ids,
+    # distances and counters stay bit-exact at its own index.  Batches larger
+    # than the sort's 4,096 buckets and 1,024 threads, few and many distinct
+    # first seeds, seed sets, per-query k and L.
+    rng = np.random.default_rng(nq + m)
+    q = np.tile(c1["queries"], (nq // len(c1["queries"]) + 1, 1))[:nq]
+    hubs = rng.choice(len(c1["base"]), n_hubs, replace=False)
+    seeds = hubs[rng.integers(0, n_hubs, (nq, m))].astype(np.int32)
+    if m > 1:
+        seeds[:, 1:][rng.random((nq, m - 1)) < 0.3] = -1
+    Ls = rng.integers(10, 97, nq).astype(np.int32)
+    ks = np.minimum(rng.integers(1, 11, nq), Ls).astype(np.int32)
+    ent = seeds if m > 1 else seeds[:, 0]
+    ids, d, ev, hp, st = search(c1["h"], q, 10, 96, W=2, entries=ent, ks=ks, Ls=Ls,
+                                flags=ann.SEARCH_GROUP_ENTRIES)
+    oi, od, oe, oh = oracle.search(c1["base"], c1["graph"], q.astype(np.float64), ent, 0, 0, W=2,
+                                   Ls=Ls, ks=ks)
+    assert st == ann.OK
+    oi_full = np.full((nq, 10), -1, np.int32)
+    oi_full[:, : oi.shape[1]] = oi
+    assert np.array_equal(ids, oi_full)
+    assert np.array_equal(ev, oe) and np.array_equal(hp, oh)
+    od_full = np.zeros((nq, 10), np.int64)
+    od_full[:, : od.shape[1]] = np.where(np.isfinite(od), od, 0).astype(np.int64)
+    valid = oi_full >= 0
+    assert np.array_equal(d[valid], od_full[valid].astype(np.int32))
+
+
+def test_grouped_work_order_with_a_bad_seed(c1):
+    # a seed out of range fails its own item only, wherever the sort put it
+    q = np.tile(c1["queries"], (30, 1))
+    seeds = np.full(len(q), c1["medoid"], np.int32)
+    seeds[1234] = len(c1["base"])
+    ids, d, ev, hp, st = search(c1["h"], q, 10, 64, entries=seeds, flags=ann.SEARCH_GROUP_ENTRIES)
+    assert st == ann.ERR_INVALID_ARG
+    assert (ids[1234] == -1).all()
+    ok = np.arange(len(q)) != 1234
+    oi, od, oe, oh = _oracle(c1, q[ok], 64, 10)
+    assert np.array_equal(ids[ok], oi) and np.array_equal(ev[ok], oe)
+
+
 def test_c1_per_query_entries_k_L(c1):
     rng = np.random.default_rng(3)
     q = c1["queries"]
@@ -216,7 +260,7 @@ def test_empty_batch_and_bad_device_inputs(c1):
     assert ann.ann_sync_status(c1["h"]) == ann.OK  # cleared by the read
     # host-side parameter checks return before any launch
     for kw in (dict(team=3), dict(team=64), dict(stage_rows=33), dict(W=5), dict(hash_bits=7), dict(hash_bits=-2),
-               dict(spill_bits=9), dict(spill_bits=17), dict(flags=8), dict(gather=2),
+               dict(spill_bits=9), dict(spill_bits=17), dict(flags=16), dict(gather=2),
                dict(entries=np.zeros((4, 33), np.int32))):
         with pytest.raises(ann.AnnError) as e:
             search(c1["h"], q[:4], 10, 64, **kw)
