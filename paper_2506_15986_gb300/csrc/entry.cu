@@ -559,8 +559,8 @@ __global__ void map_hub_seeds(const int32_t *hub_ids, int64_t nq, int m, const i
 // ballot for the first unexpanded entry, one adjacency row read by lanes
 // 0..s-1, a visited test-and-set in a per-warp shared-memory bitmap over the
 // hubs, the fresh neighbours scored lane-parallel (-q_hat . e_hat in FP32
-// over the BF16 hub rows), a 32-key bitonic sort of the new keys and a
-// bitonic merge with the pool, truncated to L.  The steps and the pool
+// over the BF16 hub rows) and inserted into the pool one by one (rank by
+// ballot, shift by shuffle), truncated to L.  The steps and the pool
 // follow the sorted-pool reading of Algorithm 1 with W = 1: the pool is the
 // L smallest keys of every hub evaluated, a hub is evaluated once, the search
 // stops when no unexpanded entry is left.  The m best pool entries become the
@@ -592,24 +592,6 @@ __device__ __forceinline__ float hub_score(const float *q, const __nv_bfloat16 *
         a3 = fmaf(f3.y, qb.w, a3);
     }
     return -((a0 + a1) + (a2 + a3));
-}
-
-// Keys of lanes [0, 32) ascending: the 32 smallest of a (ascending, one key
-// per lane) and b (ascending) in *lo, the 32 largest in *hi.  Pairwise minima
-// of a against b reversed form a bitonic sequence (the maxima another), which
-// five half-cleaner stages sort.
-__device__ __forceinline__ void merge32(uint64_t a, uint64_t b, int lane, uint64_t *lo, uint64_t *hi)
-{
-    const uint64_t rb = __shfl_sync(kFull, b, 31 - lane);
-    uint64_t mn = a < rb ? a : rb, mx = a < rb ? rb : a;
-#pragma unroll
-    for (int j = 16; j > 0; j >>= 1) {
-        const uint64_t o = __shfl_xor_sync(kFull, mn, j), p = __shfl_xor_sync(kFull, mx, j);
-        mn = (lane & j) ? kmax(mn, o) : kmin(mn, o);
-        mx = (lane & j) ? kmax(mx, p) : kmin(mx, p);
-    }
-    *lo = mn;
-    *hi = mx;
 }
 
 // NP keys per lane: pools of up to 32 * NP hubs (element r * 32 + lane in
@@ -672,17 +654,36 @@ __global__ void __launch_bounds__(32 * kNavWarps, 4)
                 if (!(atomicOr(&vis[nb >> 5], bit) & bit))
                     cand = make_key(f32_to_ord(hub_score(q, Eb + static_cast<int64_t>(nb) * 64)), nb);
             }
-            cand = warp_sort32(cand, lane);
-            // the pool keeps the L smallest keys of itself and the new ones:
-            // merge the new keys into the lower 32, the displaced ones into
-            // the next 32 (every key of pool[r + 1] is above every key of pool[r])
-            uint64_t carry = cand;
+            // the fresh keys enter the pool one at a time: a key's rank is the
+            // count of smaller pool keys (one ballot per register), the keys
+            // from that rank on move up one place and the L-th drops out, so
+            // the pool stays the L smallest keys evaluated, the set a sort
+            // and merge of all the new keys would give
+            unsigned fresh = __ballot_sync(kFull, cand != kKeyMax);
+            while (fresh) {
+                const int src = __ffs(fresh) - 1;
+                fresh &= fresh - 1;
+                const uint64_t c = __shfl_sync(kFull, cand, src);
+                int rank = 0;
 #pragma unroll
-            for (int r = 0; r < NP; ++r) {
-                uint64_t lo, hi;
-                merge32(pool[r], carry, lane, &lo, &hi);
-                pool[r] = r * 32 + lane < L ? lo : kKeyMax;
-                carry = hi;
+                for (int r = 0; r < NP; ++r)
+                    rank += __popc(__ballot_sync(kFull, pool[r] < c));
+                if (rank >= L)
+                    continue;
+                uint64_t below = c;  // what lane 0 of the next register takes
+#pragma unroll
+                for (int r = 0; r < NP; ++r) {
+                    const uint64_t up = __shfl_up_sync(kFull, pool[r], 1);
+                    const uint64_t top = __shfl_sync(kFull, pool[r], 31);
+                    const int idx = r * 32 + lane;
+                    uint64_t v = pool[r];
+                    if (idx == rank)
+                        v = c;
+                    else if (idx > rank)
+                        v = lane == 0 ? below : up;
+                    pool[r] = idx < L ? v : kKeyMax;
+                    below = top;
+                }
             }
         }
         if (lane < m_seeds) {
