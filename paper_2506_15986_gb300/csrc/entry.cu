@@ -600,15 +600,23 @@ template <int NP>
 __global__ void __launch_bounds__(32 * kNavWarps, 4)
     hub_nav_kernel(const float *qhat, int64_t nq, const __nv_bfloat16 *Eb, int H, const int32_t *hgraph, int s,
                    int32_t entry, int L, int m_seeds, const int32_t *hub_nodes, int32_t medoid, int bm_words,
-                   int32_t *out)
+                   unsigned *counter, int32_t *out)
 {
     extern __shared__ __align__(16) uint8_t nav_smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int per_warp = 256 + 4 * bm_words;
     float *q = reinterpret_cast<float *>(nav_smem + wid * per_warp);
     uint32_t *vis = reinterpret_cast<uint32_t *>(nav_smem + wid * per_warp + 256);
-    for (int64_t qi = blockIdx.x * static_cast<int64_t>(kNavWarps) + wid; qi < nq;
-         qi += static_cast<int64_t>(gridDim.x) * kNavWarps) {
+    for (;;) {
+        // the next query from the launch's work queue (the grid holds only
+        // resident warps, so the batch's last queries go to whichever warps
+        // finish first)
+        unsigned u = 0;
+        if (lane == 0)
+            u = atomicAdd(counter, 1u);
+        const int64_t qi = __shfl_sync(kFull, u, 0);
+        if (qi >= nq)
+            break;
         if (lane < 16)
             reinterpret_cast<float4 *>(q)[lane] = reinterpret_cast<const float4 *>(qhat + qi * 64)[lane];
         for (int w = lane; w < bm_words; w += 32)
@@ -1059,8 +1067,9 @@ ann_status ann_select_entries(ann_index *idx, const void *d_queries, int64_t nq,
     int32_t *hid = reinterpret_cast<int32_t *>(static_cast<uint8_t *>(scr) + qf + qb);
     float *hsc = reinterpret_cast<float *>(static_cast<uint8_t *>(scr) + qf + qb + hb);
     st = launch_tower(m, X, nq, qhat, qbf, nullptr, nullptr, nullptr, idx->d_status, s);
-    if (st == ANN_OK && L_hub <= kNavMaxPool && m->s <= 32) {
-        // the hub-graph search in one launch (pools of up to 64 hubs)
+    if (st == ANN_OK && L_hub <= kNavMaxPool && m->s <= 32 && nq <= INT32_MAX) {
+        // the hub-graph search in one launch (pools of up to 64 hubs; a
+        // 32-bit work counter)
         const int bm_words = (m->H + 127) / 128 * 4;
         const size_t per_warp = 256 + 4 * static_cast<size_t>(bm_words);
         const size_t smem = per_warp * kNavWarps;
@@ -1068,12 +1077,20 @@ ann_status ann_select_entries(ann_index *idx, const void *d_queries, int64_t nq,
         cudaError_t e =
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
         if (e == cudaSuccess) {
+            // a persistent grid of the CTAs that fit at once
+            int per_sm = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * kNavWarps, smem);
             const int64_t blocks = std::min<int64_t>((nq + kNavWarps - 1) / kNavWarps,
-                                                     static_cast<int64_t>(idx->num_sms) * 8);
-            kern<<<static_cast<unsigned>(blocks), 32 * kNavWarps, smem, s>>>(
-                qhat, nq, m->Eb, m->H, m->hub_graph, m->s, m->hub_entry, L_hub, m_seeds, m->hub_nodes, idx->medoid,
-                bm_words, d_entry);
-            e = cudaGetLastError();
+                                                     static_cast<int64_t>(idx->num_sms) * std::max(per_sm, 1));
+            unsigned *counter = reinterpret_cast<unsigned *>(static_cast<uint8_t *>(scr) + qf + qb + 2 * hb);
+            if (e == cudaSuccess)
+                e = cudaMemsetAsync(counter, 0, 4, s);
+            if (e == cudaSuccess) {
+                kern<<<static_cast<unsigned>(blocks), 32 * kNavWarps, smem, s>>>(
+                    qhat, nq, m->Eb, m->H, m->hub_graph, m->s, m->hub_entry, L_hub, m_seeds, m->hub_nodes,
+                    idx->medoid, bm_words, counter, d_entry);
+                e = cudaGetLastError();
+            }
         }
         st = cuda_status(e);
     } else if (st == ANN_OK) {
