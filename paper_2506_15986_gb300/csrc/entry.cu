@@ -279,35 +279,78 @@ __global__ void __launch_bounds__(128)
 // tower_forward_kernel, q_hat written as BF16 straight into the canonical A
 // tile of the hub GEMM (never through global memory), then the hubs in tiles
 // of 256 with two B buffers and two TMEM accumulators, so that one tile's
-// epilogue overlaps the next tile's staging and MMA.  Scores, ties and the
+// epilogue overlaps the next tile's load and MMA.  Scores, ties and the
 // top-M rule are those of hub_argmax_kernel.
+// The weight and hub operands arrive as whole 32 KB canonical images
+// (packed once per model) by one bulk copy each (cp.async.bulk, completion
+// counted on an mbarrier), issued by thread 0: W2 and the first two hub
+// tiles at the start, each W1 chunk as soon as the MMA before it has read
+// the buffer, each later hub tile as soon as the MMA two tiles back has.
+// Only the queries are staged by the threads (FP32 to BF16).
 //   shared memory: sA 16 KB (GEMM 1 A chunks, then the q_hat tile), sB 32 KB
-//   (GEMM 1 B chunks, then W2^T), sH 64 KB (the hidden layer, then the two
-//   256 x 64 hub tiles); 120 KB in all keeps one CTA per SM, which owns all
-//   512 TMEM columns.
-constexpr int kEntrySmem = 120 * 1024;
+//   (W1 chunks), sH 64 KB (the hidden layer), sW 32 KB (W2), sE 64 KB (two
+//   hub tiles), then the barriers: 208 KB keeps one CTA per SM, which owns
+//   all 512 TMEM columns.
+constexpr int kEntrySmem = 212992 + 64;
+
+struct EntryBars {
+    uint64_t mma[2];  // MMA commits (accumulator 0 / 1)
+    uint64_t w1, w2;  // W1 chunk and W2 image loads
+    uint64_t e[2];    // hub tile loads (buffer 0 / 1)
+};
 
 template <int M>
 __global__ void __launch_bounds__(128)
-    entry_exhaustive_kernel(const TowerArgs t, const __nv_bfloat16 *Eb, int H, const int32_t *hub_nodes,
+    entry_exhaustive_kernel(const TowerArgs t, const uint8_t *packed, int H, const int32_t *hub_nodes,
                             int32_t *out_node)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t *sA = smem;
     uint8_t *sB = smem + 16384;
     uint8_t *sH = smem + 49152;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 114688);  // bar[0], bar[1]
-    uint32_t *slot = reinterpret_cast<uint32_t *>(smem + 114688 + 16);
+    uint8_t *sW = smem + 114688;
+    uint8_t *sE = smem + 147456;
+    EntryBars *bars = reinterpret_cast<EntryBars *>(smem + 212992);
+    uint32_t *slot = reinterpret_cast<uint32_t *>(smem + 212992 + sizeof(EntryBars));
+    int *sfail = reinterpret_cast<int *>(smem + 212992 + sizeof(EntryBars) + 4);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m = warp * 32 + lane;
     const int64_t r0 = static_cast<int64_t>(blockIdx.x) * 128;
     const int64_t row = r0 + m;
     const bool live = row < t.nq;
+    const bool leader = threadIdx.x == 0;
+    const int nc1 = (t.in_dim + 63) / 64, ntiles = (H + 255) / 256;
+    const uint8_t *pW1 = packed, *pW2 = packed + static_cast<size_t>(nc1) * 32768,
+                  *pE = packed + static_cast<size_t>(nc1 + 1) * 32768;
+    // loads issued and waited for, per load barrier (thread 0 only): every
+    // issued copy is waited for before the CTA exits
+    int w1_iss = 0, w1_wt = 0, w2_iss = 0, w2_wt = 0, e_iss[2] = {0, 0}, e_wt[2] = {0, 0};
+    auto load = [&](void *dst, const void *src, uint64_t *bar, int &issued) {
+        mbar_arrive_expect_tx(bar, 32768);
+        bulk_g2s(dst, src, 32768, bar);
+        ++issued;
+    };
+    // thread 0: wait for the next load on `bar`; on a timeout record the
+    // failure (the results are then discarded)
+    auto wait_load = [&](uint64_t *bar, int &waited) {
+        if (!mbar_wait_bounded(bar, static_cast<uint32_t>(waited & 1), kTcWaitIters))
+            *sfail = 1;
+        ++waited;
+    };
 
-    if (threadIdx.x == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+    if (leader) {
+        mbar_init(&bars->mma[0], 1);
+        mbar_init(&bars->mma[1], 1);
+        mbar_init(&bars->w1, 1);
+        mbar_init(&bars->w2, 1);
+        mbar_init(&bars->e[0], 1);
+        mbar_init(&bars->e[1], 1);
+        *sfail = 0;
         fence_mbar_init();
+        load(sB, pW1, &bars->w1, w1_iss);
+        load(sW, pW2, &bars->w2, w2_iss);
+        for (int b = 0; b < 2 && b < ntiles; ++b)
+            load(sE + b * 32768, pE + static_cast<size_t>(b) * 32768, &bars->e[b], e_iss[b]);
     }
     if (warp == 0)
         tmem_alloc(slot, 512);
@@ -317,10 +360,32 @@ __global__ void __launch_bounds__(128)
     const uint32_t tmem = *slot;
     const uint32_t my_lane = tmem + (static_cast<uint32_t>(warp * 32) << 16);
     uint32_t ph[2] = {0u, 0u};
+    bool ok = true;
 
-    // ---- the tower: GEMM 1, bias + ReLU to BF16, GEMM 2, normalisation
-    const Operand W1{t.W1t, OP_BF16, t.in_dim, 1, 256, t.in_dim, nullptr};
-    bool ok = tc_gemm_tile<256>(t.X, r0, W1, 0, t.in_dim, sA, sB, &bar[0], ph[0], tmem);
+    // ---- GEMM 1: the queries staged chunk by chunk, W1 chunks by bulk copy
+    constexpr uint32_t ID1 = idesc_bf16_f32(128, 256);
+    for (int c = 0; c < nc1 && ok; ++c) {
+        stage_tile<128, 8>(sA, t.X, r0, static_cast<int64_t>(c) * 64);
+        fence_proxy_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        if (leader) {
+            wait_load(&bars->w1, w1_wt);
+            if (*sfail) {
+                mbar_arrive(&bars->mma[0]);  // no MMA: release the waiters
+            } else {
+                tc_fence_after();
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk)
+                    tc_mma(tmem, smem_desc(sA + kk * 256, 128, 1024), smem_desc(sB + kk * 256, 128, 1024), ID1,
+                           (c > 0 || kk > 0) ? 1u : 0u);
+                tc_commit(&bars->mma[0]);
+            }
+        }
+        ok = tc_wait(&bars->mma[0], ph[0]);
+        if (ok && leader && c + 1 < nc1)
+            load(sB, pW1 + static_cast<size_t>(c + 1) * 32768, &bars->w1, w1_iss);  // sB is free again
+    }
     if (ok) {
         for (int c0 = 0; c0 < 256; c0 += 32) {
             float v[32];
@@ -334,21 +399,24 @@ __global__ void __launch_bounds__(128)
                 *reinterpret_cast<uint4 *>(sH + canon_off(m, c0 + j, 32)) = pack8_bf16(a);
             }
         }
-        const Operand W2{t.W2t, OP_BF16, 256, 1, 64, 256, nullptr};
-        stage_tile<64, 32>(sB, W2, 0, 0);
         fence_proxy_async_smem();
         tc_fence_before();
         __syncthreads();
-        if (threadIdx.x == 0) {
-            tc_fence_after();
-            constexpr uint32_t ID2 = idesc_bf16_f32(128, 64);
+        if (leader) {
+            wait_load(&bars->w2, w2_wt);
+            if (*sfail) {
+                mbar_arrive(&bars->mma[0]);
+            } else {
+                tc_fence_after();
+                constexpr uint32_t ID2 = idesc_bf16_f32(128, 64);
 #pragma unroll
-            for (int kk = 0; kk < 16; ++kk)
-                tc_mma(tmem, smem_desc(sH + kk * 256, 128, 4096), smem_desc(sB + kk * 256, 128, 4096), ID2,
-                       kk > 0 ? 1u : 0u);
-            tc_commit(&bar[0]);
+                for (int kk = 0; kk < 16; ++kk)
+                    tc_mma(tmem, smem_desc(sH + kk * 256, 128, 4096), smem_desc(sW + kk * 256, 128, 4096), ID2,
+                           kk > 0 ? 1u : 0u);
+                tc_commit(&bars->mma[0]);
+            }
         }
-        ok = tc_wait(&bar[0], ph[0]);
+        ok = tc_wait(&bars->mma[0], ph[0]);
     }
     if (ok) {
         float z[64];
@@ -382,7 +450,6 @@ __global__ void __launch_bounds__(128)
         for (int j = 0; j < 64; j += 8)
             *reinterpret_cast<uint4 *>(sA + canon_off(m, j, 8)) = pack8_bf16(z + j);
     }
-
     // ---- hub scores in tiles of 256, double buffered
     float best[M];
     int bi[M];
@@ -391,36 +458,38 @@ __global__ void __launch_bounds__(128)
         best[j] = -INFINITY;
         bi[j] = -1;
     }
-    const Operand E{Eb, OP_BF16, 64, 1, H, 64, nullptr};
-    const int ntiles = (H + 255) / 256;
     constexpr uint32_t IDH = idesc_bf16_f32(128, 256);
     auto issue = [&](int tile) {
-        // stage hub tile `tile` into buffer tile & 1 and start its MMA into
-        // accumulator tile & 1 (columns 256 * (tile & 1))
-        uint8_t *b = sH + (tile & 1) * 32768;
-        stage_tile<256, 8>(b, E, static_cast<int64_t>(tile) * 256, 0);
+        // the MMA of hub tile `tile` (buffer and accumulator tile & 1) once
+        // its image has landed
         fence_proxy_async_smem();
         tc_fence_before();
         __syncthreads();
-        if (threadIdx.x == 0) {
-            tc_fence_after();
+        if (leader) {
+            wait_load(&bars->e[tile & 1], e_wt[tile & 1]);
+            if (*sfail) {
+                mbar_arrive(&bars->mma[tile & 1]);
+            } else {
+                tc_fence_after();
+                const uint8_t *b = sE + (tile & 1) * 32768;
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk)
-                tc_mma(tmem + (tile & 1) * 256, smem_desc(sA + kk * 256, 128, 1024), smem_desc(b + kk * 256, 128, 1024),
-                       IDH, kk > 0 ? 1u : 0u);
-            tc_commit(&bar[tile & 1]);
+                for (int kk = 0; kk < 4; ++kk)
+                    tc_mma(tmem + (tile & 1) * 256, smem_desc(sA + kk * 256, 128, 1024),
+                           smem_desc(b + kk * 256, 128, 1024), IDH, kk > 0 ? 1u : 0u);
+                tc_commit(&bars->mma[tile & 1]);
+            }
         }
     };
-    if (ok) {
-        tc_fence_before();
-        __syncthreads();  // the hidden layer in sH is no longer read by GEMM 2 (waited above)
+    if (ok)
         issue(0);
-    }
     for (int tile = 0; tile < ntiles && ok; ++tile) {
         if (tile + 1 < ntiles)
             issue(tile + 1);  // overlaps this tile's wait and epilogue
-        if (!(ok = tc_wait(&bar[tile & 1], ph[tile & 1])))
+        if (!(ok = tc_wait(&bars->mma[tile & 1], ph[tile & 1])))
             break;
+        if (leader && tile + 2 < ntiles)  // this tile's buffer is free again
+            load(sE + (tile & 1) * 32768, pE + static_cast<size_t>(tile + 2) * 32768, &bars->e[tile & 1],
+                 e_iss[tile & 1]);
         const int c0 = tile * 256;
         for (int cc = 0; cc < 256 && c0 + cc < H; cc += 32) {
             float v[32];
@@ -447,12 +516,24 @@ __global__ void __launch_bounds__(128)
         }
         tc_fence_before();  // these TMEM reads end before the MMA that reuses the accumulator
     }
-    if (!ok && threadIdx.x == 0)
+    const bool failed = __syncthreads_or(leader && *sfail) || !ok;
+    if (failed && leader)
         atomicOr(t.status, kStatusTimeoutBit);
     if (live) {
 #pragma unroll
         for (int j = 0; j < M; ++j)
-            out_node[row * M + j] = (ok && bi[j] >= 0) ? hub_nodes[bi[j]] : -1;
+            out_node[row * M + j] = (!failed && bi[j] >= 0) ? hub_nodes[bi[j]] : -1;
+    }
+    if (leader) {
+        // every copy issued lands before the CTA's shared memory goes away
+        auto drain = [&](uint64_t *bar, int &waited, int issued) {
+            for (; waited < issued; ++waited)
+                mbar_wait_bounded(bar, static_cast<uint32_t>(waited & 1), kTcWaitIters);
+        };
+        drain(&bars->w1, w1_wt, w1_iss);
+        drain(&bars->w2, w2_wt, w2_iss);
+        drain(&bars->e[0], e_wt[0], e_iss[0]);
+        drain(&bars->e[1], e_wt[1], e_iss[1]);
     }
     tc_fence_before();
     __syncthreads();
@@ -463,6 +544,34 @@ __global__ void __launch_bounds__(128)
 }
 
 // ---- model preparation ------------------------------------------------------
+
+// Canonical K-major images (the layout stage_tile writes: 16-byte chunk c of
+// an image holds row (c / (8 KG)) * 8 + c % 8 and k-chunk (c / 8) % KG) of a
+// row-major BF16 matrix src [rows][cols], one 16-byte chunk per thread.
+// Image (tr, tk), at out + (tr * ntk + tk) * ROWS * KG * 16, holds rows
+// [tr * ROWS, +ROWS) x columns [tk * 8 KG, +8 KG), zero outside the matrix.
+__global__ void pack_canonical_kernel(const __nv_bfloat16 *src, int64_t rows, int cols, int ROWS, int KG, int ntr,
+                                      int ntk, uint8_t *out)
+{
+    const int64_t per = static_cast<int64_t>(ROWS) * KG;
+    const int64_t total = per * ntr * ntk;
+    const unsigned short *bits = reinterpret_cast<const unsigned short *>(src);
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < total;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t img = i / per;
+        const int c = static_cast<int>(i % per);
+        const int64_t r = (img / ntk) * ROWS + (c / (8 * KG)) * 8 + (c & 7);
+        const int64_t k = (img % ntk) * 8 * KG + ((c >> 3) % KG) * 8;
+        uint32_t w[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const uint32_t lo = (r < rows && k + 2 * j < cols) ? bits[r * cols + k + 2 * j] : 0u;
+            const uint32_t hi = (r < rows && k + 2 * j + 1 < cols) ? bits[r * cols + k + 2 * j + 1] : 0u;
+            w[j] = lo | (hi << 16);
+        }
+        reinterpret_cast<uint4 *>(out)[i] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
 
 // BF16 transposed weight copies for K-major B operands, and normalised hub
 // embeddings (FP32 and BF16)
@@ -596,8 +705,11 @@ __device__ __forceinline__ float hub_score(const float *q, const __nv_bfloat16 *
 
 // NP keys per lane: pools of up to 32 * NP hubs (element r * 32 + lane in
 // pool[r]).
+// Registers are capped for eight 8-warp CTAs per SM with one key per lane
+// (six with two): the walk is latency-bound, so resident warps count more
+// than registers (no spills at 32 and 40 registers).
 template <int NP>
-__global__ void __launch_bounds__(32 * kNavWarps, 4)
+__global__ void __launch_bounds__(32 * kNavWarps, NP == 1 ? 8 : 6)
     hub_nav_kernel(const float *qhat, int64_t nq, const __nv_bfloat16 *Eb, int H, const int32_t *hgraph, int s,
                    int32_t entry, int L, int m_seeds, const int32_t *hub_nodes, int32_t medoid, int bm_words,
                    unsigned *counter, int32_t *out)
@@ -734,6 +846,7 @@ void free_model(ann_entry_model *m)
     cudaFree(m->W2t);
     cudaFree(m->En);
     cudaFree(m->Eb);
+    cudaFree(m->packed);
     cudaFree(m->hub_nodes);
     cudaFree(m->hub_graph);
     if (m->hub_index)
@@ -741,12 +854,29 @@ void free_model(ann_entry_model *m)
     delete m;
 }
 
+size_t packed_model_bytes(int in_dim, int H)
+{
+    return static_cast<size_t>((in_dim + 63) / 64 + 1 + (H + 255) / 256) * 32768;
+}
+
 ann_status prepare_model(ann_entry_model *m, cudaStream_t s)
 {
     const int64_t total = static_cast<int64_t>(m->in_dim) * 256 + 256 * 64 + m->H;
     prepare_model_kernel<<<static_cast<unsigned>((total + 255) / 256), 256, 0, s>>>(
         m->W1, m->W2, m->E, m->in_dim, m->H, m->W1t, m->W2t, m->En, m->Eb);
-    return cuda_status(cudaGetLastError());
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && m->packed) {
+        // W1^T in 64-wide k chunks of 256 rows, W2^T (64 rows x 256), the
+        // hubs in tiles of 256 rows x 64
+        const int nc1 = (m->in_dim + 63) / 64, nt = (m->H + 255) / 256;
+        pack_canonical_kernel<<<256, 256, 0, s>>>(m->W1t, 256, m->in_dim, 256, 8, 1, nc1, m->packed);
+        pack_canonical_kernel<<<256, 256, 0, s>>>(m->W2t, 64, 256, 64, 32, 1, 1,
+                                                  m->packed + static_cast<size_t>(nc1) * 32768);
+        pack_canonical_kernel<<<256, 256, 0, s>>>(m->Eb, m->H, 64, 256, 8, nt, 1,
+                                                  m->packed + static_cast<size_t>(nc1 + 1) * 32768);
+        e = cudaGetLastError();
+    }
+    return cuda_status(e);
 }
 
 ann_status launch_tower(const ann_entry_model *m, const Operand &X, int64_t nq, float *qhat,
@@ -827,7 +957,7 @@ ann_status launch_entry_topm(const ann_entry_model *m, const Operand &X, int64_t
     if (e != cudaSuccess)
         return cuda_status(e);
     entry_exhaustive_kernel<M><<<static_cast<unsigned>((nq + 127) / 128), 128, kEntrySmem, s>>>(
-        t, m->Eb, m->H, m->hub_nodes, out_node);
+        t, m->packed, m->H, m->hub_nodes, out_node);
     return cuda_status(cudaGetLastError());
 }
 
@@ -836,6 +966,8 @@ ann_status launch_entry_exhaustive(const ann_entry_model *m, const Operand &X, i
 {
     if (nq == 0)
         return ANN_OK;
+    if (!m->packed)  // only index models carry the packed operand images
+        return ANN_ERR_INVALID_ARG;
     switch (topm) {
     case 1: return launch_entry_topm<1>(m, X, nq, qhat, out_node, status, s);
     case 2: return launch_entry_topm<2>(m, X, nq, qhat, out_node, status, s);
@@ -948,6 +1080,7 @@ ann_status ann_set_entry_model(ann_index *idx, const ann_entry_model_desc *md, v
     m->W2t = dev_alloc<__nv_bfloat16>(256 * 64, e);
     m->En = dev_alloc<float>(static_cast<size_t>(H) * 64, e);
     m->Eb = dev_alloc<__nv_bfloat16>(static_cast<size_t>(H) * 64, e);
+    m->packed = dev_alloc<uint8_t>(packed_model_bytes(m->in_dim, H), e);
     m->hub_nodes = dev_alloc<int32_t>(H, e);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(m->W1, md->W1, static_cast<size_t>(m->in_dim) * 256 * 4, cudaMemcpyDefault, s);

@@ -19,6 +19,10 @@ struct ann_entry_model {
     __nv_bfloat16 *W1t = nullptr;            // [256][in_dim]
     __nv_bfloat16 *W2t = nullptr;            // [64][256]
     __nv_bfloat16 *Eb = nullptr;             // normalised, BF16 [H][64]
+    // index models only: the operands of the exhaustive entry kernel as the
+    // 32 KB canonical shared-memory images its bulk copies load (W1 in
+    // 64-wide k chunks, then W2, then the hubs in tiles of 256 rows)
+    uint8_t *packed = nullptr;
     int32_t *hub_nodes = nullptr;            // [H] node ids
     int32_t *hub_graph = nullptr;            // [H][s]
     int32_t hub_entry = 0;
@@ -28,6 +32,10 @@ struct ann_entry_model {
 namespace ann {
 
 void free_model(ann_entry_model *m);
+// Bytes of the packed operand images of a model (32 KB per image).
+size_t packed_model_bytes(int in_dim, int H);
+// BF16 copies of the weights and normalised hub embeddings, and, when
+// m->packed is allocated, the packed operand images (stream-ordered).
 ann_status prepare_model(ann_entry_model *m, cudaStream_t s);
 ann_status build_hub_index(ann_index *idx, ann_entry_model *m, const int32_t *hub_graph, int32_t hub_entry,
                            cudaStream_t s);
