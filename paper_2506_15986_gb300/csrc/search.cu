@@ -781,12 +781,15 @@ __global__ void __launch_bounds__(32 * kMaxSearchWarps, 16) beam_search_kernel(c
 // Work order grouped by first seed: a counting sort of the work items by a
 // 12-bit hash of their first seed, in one CTA (the histogram and the scatter
 // use shared-memory atomics, so items of one bucket come out in no fixed
-// order; the search's results do not depend on the order).  Cost is linear in
-// the batch, about a microsecond per 10,000 items, against milliseconds of
-// search.
+// order; the search's results do not depend on the order).  Each thread
+// reads its items' seeds eight at a time, so their loads are in flight
+// together, and keeps the buckets of the first kGroupCache items in shared
+// memory for the scatter pass.
 constexpr int kGroupThreads = 1024;
 constexpr int kGroupBits = 12;
 constexpr int kGroupPer = (1 << kGroupBits) / kGroupThreads;  // buckets per thread
+constexpr int kGroupBatch = 8;                                 // seeds loaded together per thread
+constexpr int kGroupCache = 12288;                             // items whose bucket is kept
 
 __device__ __forceinline__ uint32_t seed_bucket(int32_t e)
 {
@@ -799,12 +802,31 @@ __global__ void __launch_bounds__(kGroupThreads)
 {
     __shared__ int cnt[1 << kGroupBits];
     __shared__ int wsum[kGroupThreads / 32];
+    __shared__ uint16_t bucket_of[kGroupCache];
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
     for (int i = t; i < (1 << kGroupBits); i += kGroupThreads)
         cnt[i] = 0;
     __syncthreads();
-    for (int64_t w = t; w < nitems; w += kGroupThreads)
-        atomicAdd(&cnt[seed_bucket(__ldg(entries + w * n_entries))], 1);
+    // item w = base + j * kGroupThreads + t for j < kGroupBatch
+    constexpr int64_t kStride = static_cast<int64_t>(kGroupThreads) * kGroupBatch;
+    for (int64_t base = 0; base < nitems; base += kStride) {
+        int32_t e[kGroupBatch];
+#pragma unroll
+        for (int j = 0; j < kGroupBatch; ++j) {
+            const int64_t w = base + j * kGroupThreads + t;
+            e[j] = w < nitems ? __ldg(entries + w * n_entries) : 0;
+        }
+#pragma unroll
+        for (int j = 0; j < kGroupBatch; ++j) {
+            const int64_t w = base + j * kGroupThreads + t;
+            if (w < nitems) {
+                const uint32_t bk = seed_bucket(e[j]);
+                atomicAdd(&cnt[bk], 1);
+                if (w < kGroupCache)
+                    bucket_of[w] = static_cast<uint16_t>(bk);
+            }
+        }
+    }
     __syncthreads();
     // exclusive scan: thread t owns buckets [kGroupPer t, kGroupPer (t + 1))
     int v[kGroupPer], tot = 0;
@@ -841,9 +863,19 @@ __global__ void __launch_bounds__(kGroupThreads)
         run += v[j];
     }
     __syncthreads();
-    for (int64_t w = t; w < nitems; w += kGroupThreads) {
-        const int pos = atomicAdd(&cnt[seed_bucket(__ldg(entries + w * n_entries))], 1);
-        order[pos] = static_cast<int32_t>(w);
+    for (int64_t base = 0; base < nitems; base += kStride) {
+        uint32_t bk[kGroupBatch];
+#pragma unroll
+        for (int j = 0; j < kGroupBatch; ++j) {
+            const int64_t w = base + j * kGroupThreads + t;
+            bk[j] = w >= nitems ? 0u : w < kGroupCache ? bucket_of[w] : seed_bucket(__ldg(entries + w * n_entries));
+        }
+#pragma unroll
+        for (int j = 0; j < kGroupBatch; ++j) {
+            const int64_t w = base + j * kGroupThreads + t;
+            if (w < nitems)
+                order[atomicAdd(&cnt[bk[j]], 1)] = static_cast<int32_t>(w);
+        }
     }
 }
 
