@@ -283,15 +283,18 @@ __global__ void __launch_bounds__(128)
 // top-M rule are those of hub_argmax_kernel.
 // The weight and hub operands arrive as whole 32 KB canonical images
 // (packed once per model) by one bulk copy each (cp.async.bulk, completion
-// counted on an mbarrier), issued by thread 0: W2 and the first two hub
-// tiles at the start, each W1 chunk as soon as the MMA before it has read
-// the buffer, each later hub tile as soon as the MMA two tiles back has.
-// Only the queries are staged by the threads (FP32 to BF16).
+// counted on an mbarrier), issued by thread 0 as soon as their buffer is
+// free: each W1 chunk when the MMA before it has read sB, W2 into sB when
+// GEMM 1 is done (the load overlaps the GEMM 1 epilogue), the first two hub
+// tiles into sH when GEMM 2 is done (overlapping the normalisation), each
+// later hub tile when the MMA two tiles back has read its buffer.  Only the
+// queries are staged by the threads (FP32 to BF16).
 //   shared memory: sA 16 KB (GEMM 1 A chunks, then the q_hat tile), sB 32 KB
-//   (W1 chunks), sH 64 KB (the hidden layer), sW 32 KB (W2), sE 64 KB (two
-//   hub tiles), then the barriers: 208 KB keeps one CTA per SM, which owns
-//   all 512 TMEM columns.
-constexpr int kEntrySmem = 212992 + 64;
+//   (W1 chunks, then W2), sH 64 KB (the hidden layer, then the two hub
+//   tiles), then the barriers: 112 KB, so that the CTA finds room on an SM
+//   that search CTAs of another stream still half occupy; it owns all 512
+//   TMEM columns, so one runs per SM.
+constexpr int kEntrySmem = 114688 + 64;
 
 struct EntryBars {
     uint64_t mma[2];  // MMA commits (accumulator 0 / 1)
@@ -308,11 +311,11 @@ __global__ void __launch_bounds__(128)
     uint8_t *sA = smem;
     uint8_t *sB = smem + 16384;
     uint8_t *sH = smem + 49152;
-    uint8_t *sW = smem + 114688;
-    uint8_t *sE = smem + 147456;
-    EntryBars *bars = reinterpret_cast<EntryBars *>(smem + 212992);
-    uint32_t *slot = reinterpret_cast<uint32_t *>(smem + 212992 + sizeof(EntryBars));
-    int *sfail = reinterpret_cast<int *>(smem + 212992 + sizeof(EntryBars) + 4);
+    uint8_t *sW = sB;  // W2 after GEMM 1
+    uint8_t *sE = sH;  // the hub tiles after GEMM 2
+    EntryBars *bars = reinterpret_cast<EntryBars *>(smem + 114688);
+    uint32_t *slot = reinterpret_cast<uint32_t *>(smem + 114688 + sizeof(EntryBars));
+    int *sfail = reinterpret_cast<int *>(smem + 114688 + sizeof(EntryBars) + 4);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m = warp * 32 + lane;
     const int64_t r0 = static_cast<int64_t>(blockIdx.x) * 128;
@@ -348,9 +351,6 @@ __global__ void __launch_bounds__(128)
         *sfail = 0;
         fence_mbar_init();
         load(sB, pW1, &bars->w1, w1_iss);
-        load(sW, pW2, &bars->w2, w2_iss);
-        for (int b = 0; b < 2 && b < ntiles; ++b)
-            load(sE + b * 32768, pE + static_cast<size_t>(b) * 32768, &bars->e[b], e_iss[b]);
     }
     if (warp == 0)
         tmem_alloc(slot, 512);
@@ -383,8 +383,12 @@ __global__ void __launch_bounds__(128)
             }
         }
         ok = tc_wait(&bars->mma[0], ph[0]);
-        if (ok && leader && c + 1 < nc1)
-            load(sB, pW1 + static_cast<size_t>(c + 1) * 32768, &bars->w1, w1_iss);  // sB is free again
+        if (ok && leader) {  // sB is free again: the next W1 chunk, or W2 after the last
+            if (c + 1 < nc1)
+                load(sB, pW1 + static_cast<size_t>(c + 1) * 32768, &bars->w1, w1_iss);
+            else
+                load(sW, pW2, &bars->w2, w2_iss);
+        }
     }
     if (ok) {
         for (int c0 = 0; c0 < 256; c0 += 32) {
@@ -417,6 +421,9 @@ __global__ void __launch_bounds__(128)
             }
         }
         ok = tc_wait(&bars->mma[0], ph[0]);
+        if (ok && leader)  // the hidden layer is read: the first two hub tiles into sH
+            for (int b = 0; b < 2 && b < ntiles; ++b)
+                load(sE + b * 32768, pE + static_cast<size_t>(b) * 32768, &bars->e[b], e_iss[b]);
     }
     if (ok) {
         float z[64];
