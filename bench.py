@@ -118,19 +118,17 @@ WORKLOADS = {
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one headline
-# search launch, from an ncu capture of this bench's timed steps; it counts
-# only while the search kernel's sources are the ones it was taken on.
+# search launch, from an ncu capture of this bench's capture sequence; it
+# counts only while the search kernel's sources are the ones it was taken on.
 MEASURED_TRAFFIC = {
     # DRAM bytes read + written per headline launch, valid for these kernel
-    # sources, entry mode, L, batch and tuned sizes (spill_bits 0: the
-    # default for L).  Captured on one launch of the same kernel and tuned
-    # sizes at L = 93 with entries of a one-epoch model (4.544 GB read,
-    # 0.806 GB written for 6.215 GB of algorithmic bytes) and scaled by the
-    # algorithmic bytes to the headline launch (5.167 GB).
+    # sources, entry mode, L, batch and tuned sizes: the mean of the three
+    # searches of a capture sequence (bench.py --capture) on the fully
+    # trained headline, 2.921 GB read and 0.005-0.010 GB written each.
     "shift": [
-        dict(digest="12c2cd3eb4cfce87", entry="exhaustive", L=93, nq=10_000, hash_bits=-1, stage_rows=8,
-             team=4, spill_bits=0, gather=0, visited_l2=False, group_entries=False,
-             bytes=(4.544243e9 + 0.806115e9) * 5.167231e9 / 6.215410e9),
+        dict(digest="25b45d1fbcd4631a", entry="exhaustive", L=93, nq=10_000, hash_bits=-1, stage_rows=8,
+             team=4, spill_bits=12, gather=0, visited_l2=True, group_entries=True,
+             bytes=((2.9226e9 + 0.0048e9) + (2.9206e9 + 0.0075e9) + (2.9194e9 + 0.0104e9)) / 3),
     ],
 }
 
@@ -171,6 +169,9 @@ def parse():
     ap.add_argument("--cand", type=int, default=64, help="hubs searched per training query")
     ap.add_argument("--l-hub", type=int, default=32)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--capture", action="store_true",
+                    help="run the first measured mode's search in a fixed sequence for a profiler capture "
+                         "(NVTX ranges 'prime' and 'capture') instead of the timed protocol")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--W", type=int, default=4, help="pool entries expanded per search step")
     ap.add_argument("--no-tune", action="store_true", help="skip ann_autotune at L*")
@@ -715,6 +716,42 @@ def timed(run, torch, ann, args, L, world, dev, nvtx=None, lanes=1):
     return total_ms, search_ms, clk.summary()
 
 
+def capture_sequence(run, torch, L, lanes):
+    """A fixed launch sequence for a profiler capture of the search at L with
+    the tuned sizes (no timing protocol): one step in the NVTX range 'prime',
+    a release of persisting L2 lines, six steps over the lanes one at a time,
+    then three steps one at a time in the NVTX range 'capture'.  Under ncu the
+    first profiled kernel of a session disturbs the persisting-L2 set-aside
+    until the next release, so profiling 'prime' and then 'capture' sees the
+    captured searches in the L2 state they run in without a profiler.
+    Returns the captured searches' event times (ms)."""
+    ls = run.lanes(lanes)
+    n = len(ls)
+    q = run.W["q"]
+    torch.cuda.nvtx.range_push("prime")
+    ls[0].step(L)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    release_l2(run)
+    for i in range(6):
+        ls[i % n].step(L)
+        torch.cuda.synchronize()
+    times = []
+    torch.cuda.nvtx.range_push("capture")
+    for i in range(3):
+        r = ls[i % n]
+        e = r.select(q)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(r.stream)
+        r.search(q, e, L)
+        e1.record(r.stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    torch.cuda.nvtx.range_pop()
+    release_l2(run)
+    return times
+
+
 def release_l2(run):
     """L2 lines left persisting by searches with the visited tables kept in
     L2 go back to normal, so that the next timed segment (another mode or
@@ -1009,6 +1046,17 @@ def run_gpu(args):
         modes = [m for m in modes if m in args.modes.split(",")]
     for mode in modes:
         res[mode] = measure_mode(Runner(W, torch, ann, args, mode), torch, ann, W, args, targets)
+    if args.capture:
+        # a profiler capture of the first measured mode's search instead of
+        # the timed protocol
+        mode = next(iter(res))
+        r = res[mode]
+        t = capture_sequence(r["run"], torch, r["L"], args.lanes)
+        if rank == 0:
+            print(json.dumps({"capture": mode, "L": r["L"], "search_ms": t, "tuned": r["tune"],
+                              "evals_per_query": r["evals"], "hops_per_query": r["hops"],
+                              "alg_bytes_per_launch": r["alg_bytes"], "kernel_digest": kernel_digest()}))
+        return
     # a short timing of every mode picks the headline: the faster learned mode
     # (hub-graph search or exhaustive tensor-core hub scoring), medoid without
     # a model; then the headline is timed under the full protocol

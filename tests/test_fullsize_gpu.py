@@ -39,9 +39,10 @@ def full():
     ann.ann_free_index(h)
 
 
-def _lanes(full, entries, m, gather=1, l2=False):
-    p = ann.search_params(K, L, W=W, hash_bits=-1, stage_rows=8, team=4, n_entries=m, gather=gather,
-                          spill_bits=12 if l2 else 0, flags=ann.SEARCH_VISITED_L2 if l2 else 0)
+def _lanes(full, entries, m, gather=1, l2=False, extra=0, stage_rows=8):
+    flags = (ann.SEARCH_VISITED_L2 if l2 else 0) | extra
+    p = ann.search_params(K, L, W=W, hash_bits=-1, stage_rows=stage_rows, team=4, n_entries=m, gather=gather,
+                          spill_bits=12 if l2 else 0, flags=flags)
     streams = [torch.cuda.Stream(device=DEV) for _ in range(3)]
     outs = []
     torch.cuda.synchronize()
@@ -65,20 +66,23 @@ def _recall(ids, gt):
     return np.mean([len(set(a) & set(b)) / K for a, b in zip(ids, gt)])
 
 
-@pytest.mark.parametrize("seeds,gather,l2", [(0, 1, False), (2, 1, False), (0, 4, True)])
-def test_full_size_sampled_parity(full, seeds, gather, l2):
+@pytest.mark.parametrize("seeds,gather,l2,extra,stage_rows", [
+    (0, 1, False, 0, 8), (2, 1, False, 0, 8), (0, 4, True, 0, 8),
+    (1, 1, True, ann.SEARCH_GROUP_ENTRIES, 8)])
+def test_full_size_sampled_parity(full, seeds, gather, l2, extra, stage_rows):
     # l2: the tuned headline's 2^12-slot first-level visited tables kept
-    # resident in L2 (ANN_SEARCH_VISITED_L2)
+    # resident in L2 (ANN_SEARCH_VISITED_L2); extra: the work order grouped
+    # by entry (ANN_SEARCH_GROUP_ENTRIES)
     rng = np.random.default_rng(11 + seeds)
     if seeds:
         ent_np = rng.integers(0, N, size=(NQ, seeds)).astype(np.int32)
-        ent = torch.from_numpy(ent_np).to(DEV)
+        ent = torch.from_numpy(ent_np if seeds > 1 else ent_np[:, 0].copy()).to(DEV)
     else:
         ent_np, ent = None, None
-    ids, dd, st = _lanes(full, ent, seeds, gather, l2)
+    ids, dd, st = _lanes(full, ent, seeds if seeds > 1 else 0, gather, l2, extra, stage_rows)
     sample = np.sort(rng.choice(NQ, 200, replace=False))
     q64 = full["w"]["queries"][sample].astype(np.float64)
-    e = full["med"] if ent_np is None else ent_np[sample]
+    e = full["med"] if ent_np is None else (ent_np[sample] if seeds > 1 else ent_np[sample, 0])
     oi, od, oe, oh = oracle.search(full["w"]["base"], full["graph"], q64, e, L, K, W=W)
     gi, gd = ids[sample], dd[sample].astype(np.float64)
     same = gi == oi
