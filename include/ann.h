@@ -138,21 +138,21 @@ typedef struct {
  *             tables of all the launch's teams fit the device's persisting-L2
  *             capacity, the search launches with an access-policy window that
  *             keeps them resident in L2 (no write-back, and compare-and-swaps
- *             that hit in L2); otherwise it launches without one.  The first
- *             such call on a device outside stream capture raises the
- *             context's persisting-L2 set-aside (cudaLimitPersistingL2CacheSize)
- *             to the device maximum.  While the set-aside is raised, accesses
+ *             that hit in L2); otherwise it launches without one.  Such a
+ *             call outside stream capture raises the context's persisting-L2
+ *             set-aside (cudaLimitPersistingL2CacheSize) to the device maximum
+ *             when it is below that.  While the set-aside is raised, accesses
  *             without a persisting window use only the rest of L2, and the
  *             persisting lines outlive the call: ann_release_l2 undoes both.
  *             ANN_SEARCH_GROUP_ENTRIES (speed only): with entries given, the
-             launch first sorts the work items by a hash of their first seed
-             (one extra single-CTA kernel, 4 bytes of scratch per item) and
-             the persistent teams take them in that order, so queries that
-             start at the same node run side by side and share the rows of
-             their first steps in L2.  Every item's outputs are written at its
-             own index and do not depend on the order.  Ignored with the
-             medoid entry (d_entry NULL).
-             ANN_SEARCH_FAULT_WAIT: fault injection for testing; every wait
+ *             launch first sorts the work items by a hash of their first seed
+ *             (one extra single-CTA kernel, 4 bytes of scratch per item) and
+ *             the persistent teams take them in that order, so queries that
+ *             start at the same node run side by side and share the rows of
+ *             their first steps in L2.  Every item's outputs are written at its
+ *             own index and do not depend on the order.  Ignored with the
+ *             medoid entry (d_entry NULL).
+ *             ANN_SEARCH_FAULT_WAIT: fault injection for testing; every wait
  *             for a round of gathered rows gives up at once, as if its time
  *             limit had passed: each query fails with -1 ids and the call
  *             reports ANN_ERR_TIMEOUT through ann_sync_status.  The copies in
