@@ -684,14 +684,16 @@ __global__ void map_hub_seeds(const int32_t *hub_ids, int64_t nq, int m, const i
 constexpr int kNavWarps = 8;
 constexpr int kNavMaxPool = 64;
 
-__device__ __forceinline__ float hub_score(const float *q, const __nv_bfloat16 *row)
+// <q, e> over NC 16-byte chunks (8 coordinates each) of a BF16 hub row, with
+// four FP32 accumulators over coordinates j mod 4
+template <int NC>
+__device__ __forceinline__ float hub_dot(const float *q, const __nv_bfloat16 *row)
 {
-    // -<q, e> with four FP32 accumulators over coordinates j mod 4
     const uint4 *r4 = reinterpret_cast<const uint4 *>(row);
     const float4 *q4 = reinterpret_cast<const float4 *>(q);
     float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
 #pragma unroll 4
-    for (int c = 0; c < 8; ++c) {
+    for (int c = 0; c < NC; ++c) {
         const uint4 x = __ldg(r4 + c);
         const float4 qa = q4[2 * c], qb = q4[2 * c + 1];
         const float2 f0 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&x.x));
@@ -707,8 +709,11 @@ __device__ __forceinline__ float hub_score(const float *q, const __nv_bfloat16 *
         a2 = fmaf(f3.x, qb.z, a2);
         a3 = fmaf(f3.y, qb.w, a3);
     }
-    return -((a0 + a1) + (a2 + a3));
+    return (a0 + a1) + (a2 + a3);
 }
+
+// -<q, e> over the whole 64-coordinate row
+__device__ __forceinline__ float hub_score(const float *q, const __nv_bfloat16 *row) { return -hub_dot<8>(q, row); }
 
 // NP keys per lane: pools of up to 32 * NP hubs (element r * 32 + lane in
 // pool[r]).
@@ -774,12 +779,29 @@ __global__ void __launch_bounds__(32 * kNavWarps, NP == 1 ? 8 : 6)
                     node = v;
             }
             __syncwarp();
-            const int32_t nb = lane < s ? __ldg(hgraph + static_cast<int64_t>(node) * s + lane) : -1;
             uint64_t cand = kKeyMax;
-            if (nb >= 0 && nb < H) {
-                const uint32_t bit = 1u << (nb & 31);
-                if (!(atomicOr(&vis[nb >> 5], bit) & bit))
-                    cand = make_key(f32_to_ord(hub_score(q, Eb + static_cast<int64_t>(nb) * 64)), nb);
+            if (s <= 16) {
+                // two lanes per neighbour (j and j + 16), 32 coordinates each:
+                // the whole warp scores instead of s lanes
+                const int j = lane & 15, half = lane >> 4;
+                const int32_t nb = j < s ? __ldg(hgraph + static_cast<int64_t>(node) * s + j) : -1;
+                bool fresh = false;
+                if (half == 0 && nb >= 0 && nb < H) {
+                    const uint32_t bit = 1u << (nb & 31);
+                    fresh = !(atomicOr(&vis[nb >> 5], bit) & bit);
+                }
+                fresh = __shfl_sync(kFull, fresh, j);
+                float part = fresh ? hub_dot<4>(q + 32 * half, Eb + static_cast<int64_t>(nb) * 64 + 32 * half) : 0.f;
+                part += __shfl_xor_sync(kFull, part, 16);
+                if (half == 0 && fresh)
+                    cand = make_key(f32_to_ord(-part), nb);
+            } else {
+                const int32_t nb = lane < s ? __ldg(hgraph + static_cast<int64_t>(node) * s + lane) : -1;
+                if (nb >= 0 && nb < H) {
+                    const uint32_t bit = 1u << (nb & 31);
+                    if (!(atomicOr(&vis[nb >> 5], bit) & bit))
+                        cand = make_key(f32_to_ord(hub_score(q, Eb + static_cast<int64_t>(nb) * 64)), nb);
+                }
             }
             // the fresh keys enter the pool one at a time: a key's rank is the
             // count of smaller pool keys (one ballot per register), the keys
