@@ -59,3 +59,15 @@ def test_batch10m_spec(monkeypatch):
     assert spec["n"] == 10_000_000 and spec["dim"] == 96 and spec["nq"] == 100_000
     assert spec["insert"] == (1_000_000, 1_000_000) and spec["gt_rows"] == 5_000
     assert spec["batching"] and spec["hubs"] == 16384
+
+
+def test_capture_and_knob_options(monkeypatch):
+    monkeypatch.setattr("sys.argv", ["bench.py", "--capture", "--fixed-L", "93", "--knobs=-1,8,4,12,0,1,1",
+                                     "--modes", "exhaustive"])
+    args = bench.parse()
+    assert args.capture and args.knobs == "-1,8,4,12,0,1,1" and args.spec["fixed_L"] == 93
+    # the stored headline traffic names every speed knob the bench matches on
+    for mt in bench.MEASURED_TRAFFIC["shift"]:
+        for key in ("digest", "entry", "L", "nq", "hash_bits", "stage_rows", "team", "spill_bits", "gather",
+                    "visited_l2", "group_entries", "bytes"):
+            assert key in mt, key
