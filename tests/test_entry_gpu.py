@@ -166,7 +166,7 @@ def test_nav_search_matches_oracle(setup, L_hub):
     assert (chosen == oi[:, 0]).mean() >= 0.99
     # a greedy walk is path dependent: a q_hat that differs in the last bits
     # can end it at another local optimum, so the few differing choices are
-    # judged in aggregate: the oracle's scores of the GPU's choices average
+    # compared in aggregate: the oracle's scores of the GPU's choices average
     # within 1e-4 of those of its own
     S = ref_q @ Eb.astype(np.float64).T
     r = np.arange(len(S))
