@@ -129,6 +129,11 @@ MEASURED_TRAFFIC = {
         dict(digest="25b45d1fbcd4631a", entry="exhaustive", L=93, nq=10_000, hash_bits=-1, stage_rows=8,
              team=4, spill_bits=12, gather=0, visited_l2=True, group_entries=True,
              bytes=((2.9226e9 + 0.0048e9) + (2.9206e9 + 0.0075e9) + (2.9194e9 + 0.0104e9)) / 3),
+        # the same with the plain work order (the autotuner picks either; grouping
+        # lets queries with one entry hub share their first rows in L2)
+        dict(digest="25b45d1fbcd4631a", entry="exhaustive", L=93, nq=10_000, hash_bits=-1, stage_rows=8,
+             team=4, spill_bits=12, gather=0, visited_l2=True, group_entries=False,
+             bytes=((3.3604e9 + 0.0056e9) + (3.3585e9 + 0.0086e9) + (3.3574e9 + 0.0119e9)) / 3),
     ],
 }
 
@@ -168,6 +173,11 @@ def parse():
     ap.add_argument("--tau", type=float, default=0.07)
     ap.add_argument("--cand", type=int, default=64, help="hubs searched per training query")
     ap.add_argument("--l-hub", type=int, default=32)
+    ap.add_argument("--hub-seeds", type=int, default=0,
+                    help="hubs in the sample the hub-graph search starts from (0: the entry hub alone)")
+    ap.add_argument("--nav-sweep", default="",
+                    help="comma list of L_hub:sample pairs: the hub-graph mode measured at each (its L*, "
+                         "evaluations, QPS with the exhaustive mode's tuned sizes, entry selection time)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--capture", action="store_true",
                     help="run the first measured mode's search in a fixed sequence for a profiler capture "
@@ -864,6 +874,56 @@ def measure_mode(run, torch, ann, W, args, targets):
                 entries=None if run.mode == "medoid" else run.entry.cpu().numpy())
 
 
+def set_hub_sample(W, ann, synth, n):
+    """The hub-graph search starts from n hubs drawn at random (0: the entry hub)."""
+    ann.ann_set_hub_seeds(W["h"], synth.hub_sample(W["H"], n) if n > 0 else None)
+
+
+def entry_ms(run, torch, reps=20):
+    """Mean CUDA-event time of one entry selection of the batch, alone."""
+    q = run.W["q"]
+    run.select(q)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(run.stream)
+    for _ in range(reps):
+        run.select(q)
+    e1.record(run.stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def nav_sweep(W, torch, ann, synth, args, dev, targets, ref):
+    """The hub-graph entry mode at several (L_hub, start sample) pairs: L* by
+    the sweep, then the timed protocol with the reference mode's tuned search
+    sizes (speed-only knobs, picked at a nearby L)."""
+    out = []
+    l_hub0 = args.l_hub
+    for item in args.nav_sweep.split(","):
+        lh, _, ns = item.partition(":")
+        args.l_hub = int(lh)
+        set_hub_sample(W, ann, synth, int(ns or 0))
+        run = Runner(W, torch, ann, args, "learned")
+        Lstar, _, per = sweep(run, torch, ann, W, targets)
+        if ref["run"].tuned.get(ref["L"]) is not None:
+            p = ref["run"].tuned[ref["L"]]
+            q = run.params(Lstar)
+            q.hash_bits, q.stage_rows, q.team, q.spill_bits, q.gather, q.flags = (
+                p.hash_bits, p.stage_rows, p.team, p.spill_bits, p.gather, p.flags)
+            run.tuned[Lstar] = q
+        run.step(Lstar, stats=True)
+        torch.cuda.synchronize()
+        st = run.stats.cpu().numpy().astype(np.int64)
+        tm, _, _ = timed(run, torch, ann, argparse.Namespace(warmup=3, steps=100), Lstar, 1, dev,
+                         lanes=args.lanes)
+        out.append(dict(l_hub=args.l_hub, sample=int(ns or 0), L=Lstar,
+                        recall=recall(run.ids.cpu().numpy(), W["gt"], run.k),
+                        evals=float(st[:, 0].mean()), qps=run.nq * 100 / (tm / 1e3),
+                        entry_ms=entry_ms(run, torch)))
+    args.l_hub = l_hub0
+    set_hub_sample(W, ann, synth, args.hub_seeds)
+    return out
+
+
 def precision_report(W, torch, ann, args, dev):
     """fp16 storage and int8 storage with a per-row scale, each with and
     without the exact fp32 rerank, against fp32 storage (k = 10 and 100), with
@@ -1037,6 +1097,9 @@ def run_gpu(args):
     ann.load_library()
     W = build_workload(args, torch, ann, synth, dev)
     learned = build_learned(W, args, torch, ann, synth, dev) if spec["learned"] else None
+    if learned:
+        W["H"] = learned["H"]
+        set_hub_sample(W, ann, synth, args.hub_seeds)
     targets = spec["targets"]
 
     res = {}
@@ -1091,6 +1154,8 @@ def run_gpu(args):
     batching = batch_report(W, torch, ann, args, dev, ["medoid"] + ([head] if head != "medoid" else [])) \
         if spec.get("batching") else None
     tpos = tpos_report(W, torch, ann, synth, args, dev) if args.tpos_sweep and spec["learned"] else None
+    navs = nav_sweep(W, torch, ann, synth, args, dev, targets, R) if args.nav_sweep and spec["learned"] \
+        else None
     peak, peak_kind = peaks()
     n_lanes = len(R["run"].lanes(args.lanes))
     # one lane: a search launch's own event span; several: consecutive
@@ -1116,11 +1181,11 @@ def run_gpu(args):
                "evals_per_query": R["evals"], "hops_per_query": R["hops"],
                "per_target": {str(t): v for t, v in R["per_target"].items()},
                "tuned": R["tune"], "sweep": R["sweep"], "other_entry_modes": others,
-               "l_hub": args.l_hub, "lanes": n_lanes,
+               "l_hub": args.l_hub, "hub_sample": args.hub_seeds, "lanes": n_lanes,
                "l2": "inputs larger than L2 (129 MB), no flush" if big
                else "base smaller than L2: an L2-resident parity config",
                "graph_build_s": W["t_build"], "repairs": W["repairs"], "learned": learned,
-               "precision": prec, "batching": batching, "tpos_sweep": tpos,
+               "precision": prec, "batching": batching, "tpos_sweep": tpos, "nav_sweep": navs,
                "parallelism": f"replicas{world}"}
         if "medoid" in others:
             med = others["medoid"]

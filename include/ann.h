@@ -419,6 +419,24 @@ ann_status ann_get_entry_model(const ann_index *idx, float *W1, float *b1, float
                                int32_t *hub_entry);
 
 /*
+ * The sample of hubs the hub-graph search (ANN_ENTRY_LEARNED_NAV) starts
+ * from.  Algorithm 1 (Sec. 2.1) starts its pool from a random sample of the
+ * graph's nodes; on the high-tier graph of Sec. 4.3 that sample is this list.
+ *   seeds  n hub indices in [0, n_hubs) (host or device; copied), drawn by
+ *          the caller (the library draws no random numbers); repeats count
+ *          once
+ *   n      0..ANN_MAX_SEEDS; 0 goes back to the single entry hub
+ *          (ann_entry_model_desc.hub_entry)
+ * Per query, every distinct sample hub is scored and the L_hub best form the
+ * first pool.  The sample belongs to the attached model: ann_set_entry_model
+ * (and ann_trainer_attach) start the new model without one.  Blocking: waits
+ * for the device, so no entry selection of the index is in flight while the
+ * sample changes.  ANN_ERR_UNSUPPORTED without a model, ANN_ERR_INVALID_ARG
+ * for n out of range or a hub index out of range.
+ */
+ann_status ann_set_hub_seeds(ann_index *idx, const int32_t *seeds, int32_t n);
+
+/*
  * Entry node per query (Sec. 4.3: the recommended hub is the entry point).
  *   d_queries  nq*dim rows as for ann_search_batch (16-byte aligned)
  *   mode       ann_entry_mode; the learned modes need an attached model

@@ -11,6 +11,8 @@ from __future__ import annotations
 import ctypes
 import os
 
+import numpy as np
+
 PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libann.so")
 
@@ -88,6 +90,7 @@ def load_library(path: str | None = None):
         "ann_set_entry_model": ([_p, _c.POINTER(ann_entry_model_desc), _p], i32),
         "ann_get_entry_model": ([_p] + [_p] * 7 + [_c.POINTER(i32)], i32),
         "ann_select_entry": ([_p, _p, i64, i32, i32, _p, _p, _p], i32),
+        "ann_set_hub_seeds": ([_p, _p, i32], i32),
         "ann_select_entries": ([_p, _p, i64, i32, i32, i32, _p, _p, _p], i32),
         "ann_trainer_create": ([i32, i32, i32, _p, _p, _p, _p, _p, i64, _c.c_float, _c.c_float,
                                 _c.c_float, _c.c_float, _c.c_float, pp], i32),
@@ -281,6 +284,15 @@ def ann_get_entry_model(h, W1=None, b1=None, W2=None, b2=None, hub_emb=None, hub
                                               _ptr(hub_emb), _ptr(hub_nodes), _ptr(hub_graph),
                                               ctypes.byref(e)), "ann_get_entry_model")
     return e.value
+
+
+def ann_set_hub_seeds(h, seeds):
+    """Hubs the hub-graph search starts from (int32 hub indices, host or
+    device); None or an empty list goes back to the single entry hub."""
+    n = 0 if seeds is None else int(len(seeds))
+    if n and not hasattr(seeds, "data_ptr"):
+        seeds = np.ascontiguousarray(seeds, np.int32)
+    _check(load_library().ann_set_hub_seeds(h, _ptr(seeds) if n else None, n), "ann_set_hub_seeds")
 
 
 def ann_select_entry(h, queries, nq, mode, L_hub, entry_out, qhat_out=None, stream=None):

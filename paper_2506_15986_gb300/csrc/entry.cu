@@ -669,6 +669,15 @@ __global__ void map_hub_seeds(const int32_t *hub_ids, int64_t nq, int m, const i
     }
 }
 
+// Every query's seed set is the model's hub sample: out[i] = seeds[i mod n]
+// for i < ns (the nq x n seed array of the general search on the hub index).
+__global__ void broadcast_hub_seeds(const int32_t *seeds, int n, int64_t ns, int32_t *out)
+{
+    const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (i < ns)
+        out[i] = seeds[i % n];
+}
+
 // ---- hub-graph search (Sec. 4.3: Algorithm 1 on the high-tier hub graph) ----
 // One warp per query, pools of at most 32 hubs: lane i holds the i-th
 // smallest (score, hub) key of the pool (bit 0: expanded), so a step is a
@@ -715,6 +724,52 @@ __device__ __forceinline__ float hub_dot(const float *q, const __nv_bfloat16 *ro
 // -<q, e> over the whole 64-coordinate row
 __device__ __forceinline__ float hub_score(const float *q, const __nv_bfloat16 *row) { return -hub_dot<8>(q, row); }
 
+// The fresh keys of a warp (cand != kKeyMax on the lanes that hold one) enter
+// the pool one at a time: a key's rank is the count of smaller pool keys (one
+// ballot per register), the keys from that rank on move up one place and the
+// L-th drops out, so the pool stays the L smallest keys evaluated, the set a
+// sort and merge of all the new keys would give.  A key not below the pool's
+// L-th key when the insertion starts cannot enter (that key only gets
+// smaller), so such keys are dropped before the serial loop.
+template <int NP>
+__device__ __forceinline__ void nav_insert(uint64_t (&pool)[NP], uint64_t cand, int L, int lane)
+{
+    const int lr = (L - 1) >> 5, ll = (L - 1) & 31;
+    uint64_t worst = kKeyMax;  // the L-th smallest key, kKeyMax while the pool has room
+#pragma unroll
+    for (int r = 0; r < NP; ++r) {
+        const uint64_t v = __shfl_sync(kFull, pool[r], ll);
+        if (r == lr)
+            worst = v;
+    }
+    unsigned fresh = __ballot_sync(kFull, cand < worst);
+    while (fresh) {
+        const int src = __ffs(fresh) - 1;
+        fresh &= fresh - 1;
+        const uint64_t c = __shfl_sync(kFull, cand, src);
+        int rank = 0;
+#pragma unroll
+        for (int r = 0; r < NP; ++r)
+            rank += __popc(__ballot_sync(kFull, pool[r] < c));
+        if (rank >= L)
+            continue;
+        uint64_t below = c;  // what lane 0 of the next register takes
+#pragma unroll
+        for (int r = 0; r < NP; ++r) {
+            const uint64_t up = __shfl_up_sync(kFull, pool[r], 1);
+            const uint64_t top = __shfl_sync(kFull, pool[r], 31);
+            const int idx = r * 32 + lane;
+            uint64_t v = pool[r];
+            if (idx == rank)
+                v = c;
+            else if (idx > rank)
+                v = lane == 0 ? below : up;
+            pool[r] = idx < L ? v : kKeyMax;
+            below = top;
+        }
+    }
+}
+
 // NP keys per lane: pools of up to 32 * NP hubs (element r * 32 + lane in
 // pool[r]).
 // Registers are capped for eight 8-warp CTAs per SM with one key per lane
@@ -723,8 +778,8 @@ __device__ __forceinline__ float hub_score(const float *q, const __nv_bfloat16 *
 template <int NP>
 __global__ void __launch_bounds__(32 * kNavWarps, NP == 1 ? 8 : 6)
     hub_nav_kernel(const float *qhat, int64_t nq, const __nv_bfloat16 *Eb, int H, const int32_t *hgraph, int s,
-                   int32_t entry, int L, int m_seeds, const int32_t *hub_nodes, int32_t medoid, int bm_words,
-                   unsigned *counter, int32_t *out)
+                   const int32_t *start, int n_start, int L, int m_seeds, const int32_t *hub_nodes, int32_t medoid,
+                   int bm_words, unsigned *counter, int32_t *out)
 {
     extern __shared__ __align__(16) uint8_t nav_smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -746,14 +801,22 @@ __global__ void __launch_bounds__(32 * kNavWarps, NP == 1 ? 8 : 6)
         for (int w = lane; w < bm_words; w += 32)
             vis[w] = 0u;
         __syncwarp();
-        // the initial pool: the entry hub, evaluated
         uint64_t pool[NP];
 #pragma unroll
         for (int r = 0; r < NP; ++r)
             pool[r] = kKeyMax;
-        if (lane == 0) {
-            vis[entry >> 5] = 1u << (entry & 31);
-            pool[0] = make_key(f32_to_ord(hub_score(q, Eb + static_cast<int64_t>(entry) * 64)), entry);
+        {
+            // the initial pool (Algorithm 1 starts from a set of nodes): the
+            // model's hub sample, or the entry hub alone; every distinct
+            // start hub is evaluated once and the L best start the pool
+            uint64_t cand = kKeyMax;
+            if (lane < n_start) {
+                const int32_t hb = __ldg(start + lane);
+                const uint32_t bit = 1u << (hb & 31);
+                if (!(atomicOr(&vis[hb >> 5], bit) & bit))
+                    cand = make_key(f32_to_ord(hub_score(q, Eb + static_cast<int64_t>(hb) * 64)), hb);
+            }
+            nav_insert<NP>(pool, cand, L, lane);
         }
         for (;;) {
             // the first unexpanded entry in pool order
@@ -803,37 +866,7 @@ __global__ void __launch_bounds__(32 * kNavWarps, NP == 1 ? 8 : 6)
                         cand = make_key(f32_to_ord(hub_score(q, Eb + static_cast<int64_t>(nb) * 64)), nb);
                 }
             }
-            // the fresh keys enter the pool one at a time: a key's rank is the
-            // count of smaller pool keys (one ballot per register), the keys
-            // from that rank on move up one place and the L-th drops out, so
-            // the pool stays the L smallest keys evaluated, the set a sort
-            // and merge of all the new keys would give
-            unsigned fresh = __ballot_sync(kFull, cand != kKeyMax);
-            while (fresh) {
-                const int src = __ffs(fresh) - 1;
-                fresh &= fresh - 1;
-                const uint64_t c = __shfl_sync(kFull, cand, src);
-                int rank = 0;
-#pragma unroll
-                for (int r = 0; r < NP; ++r)
-                    rank += __popc(__ballot_sync(kFull, pool[r] < c));
-                if (rank >= L)
-                    continue;
-                uint64_t below = c;  // what lane 0 of the next register takes
-#pragma unroll
-                for (int r = 0; r < NP; ++r) {
-                    const uint64_t up = __shfl_up_sync(kFull, pool[r], 1);
-                    const uint64_t top = __shfl_sync(kFull, pool[r], 31);
-                    const int idx = r * 32 + lane;
-                    uint64_t v = pool[r];
-                    if (idx == rank)
-                        v = c;
-                    else if (idx > rank)
-                        v = lane == 0 ? below : up;
-                    pool[r] = idx < L ? v : kKeyMax;
-                    below = top;
-                }
-            }
+            nav_insert<NP>(pool, cand, L, lane);
         }
         if (lane < m_seeds) {
             const int32_t hub = pool[0] != kKeyMax ? key_id(pool[0]) : -1;
@@ -878,6 +911,7 @@ void free_model(ann_entry_model *m)
     cudaFree(m->packed);
     cudaFree(m->hub_nodes);
     cudaFree(m->hub_graph);
+    cudaFree(m->hub_seeds);
     if (m->hub_index)
         ann_free_index(m->hub_index);
     delete m;
@@ -1048,7 +1082,14 @@ ann_status build_hub_index(ann_index *idx, ann_entry_model *m, const int32_t *hu
         if (e != cudaSuccess)
             return cuda_status(e);
     }
-    e = cudaStreamSynchronize(s);
+    // the start list of the hub-graph search: the entry hub until a sample is set
+    if (!m->hub_seeds)
+        m->hub_seeds = dev_alloc<int32_t>(ANN_MAX_SEEDS, e);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(m->hub_seeds, &m->hub_entry, 4, cudaMemcpyHostToDevice, s);
+    m->n_hub_seeds = 0;
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(s);
     if (e != cudaSuccess)
         return cuda_status(e);
     if (m->hub_index) {
@@ -1172,6 +1213,39 @@ ann_status ann_get_entry_model(const ann_index *idx, float *W1, float *b1, float
     return cuda_status(e);
 }
 
+ann_status ann_set_hub_seeds(ann_index *idx, const int32_t *seeds, int32_t n)
+{
+    if (!idx || n < 0 || n > ANN_MAX_SEEDS || (n > 0 && !seeds))
+        return ANN_ERR_INVALID_ARG;
+    ann_entry_model *m = idx->model;
+    if (!m)
+        return ANN_ERR_UNSUPPORTED;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(idx->device);
+    int32_t h[ANN_MAX_SEEDS];
+    cudaError_t e = cudaSuccess;
+    if (n > 0)
+        e = cudaMemcpy(h, seeds, static_cast<size_t>(n) * 4, cudaMemcpyDefault);
+    else
+        h[0] = m->hub_entry;  // back to the entry hub alone
+    ann_status st = cuda_status(e);
+    for (int i = 0; st == ANN_OK && i < n; ++i)
+        if (h[i] < 0 || h[i] >= m->H)
+            st = ANN_ERR_INVALID_ARG;
+    if (st == ANN_OK) {
+        // entry selections still in flight (on any stream) read the old list
+        e = cudaDeviceSynchronize();
+        if (e == cudaSuccess)
+            e = cudaMemcpy(m->hub_seeds, h, static_cast<size_t>(std::max(n, 1)) * 4, cudaMemcpyHostToDevice);
+        st = cuda_status(e);
+    }
+    if (st == ANN_OK)
+        m->n_hub_seeds = n;
+    cudaSetDevice(prev);
+    return st;
+}
+
 ann_status ann_select_entry(ann_index *idx, const void *d_queries, int64_t nq, int32_t mode, int32_t L_hub,
                             int32_t *d_entry, float *d_qhat, void *stream)
 {
@@ -1215,11 +1289,16 @@ ann_status ann_select_entries(ann_index *idx, const void *d_queries, int64_t nq,
         cudaSetDevice(prev);
         return st;
     }
-    // scratch: q_hat fp32 + bf16, hub ids, hub scores
+    // pools of up to 64 hubs run in one launch of hub_nav_kernel (with a
+    // 32-bit work counter), larger ones in the general search on the hub index
+    const bool one_launch = L_hub <= kNavMaxPool && m->s <= 32 && nq <= INT32_MAX;
+    // scratch: q_hat fp32 + bf16, hub ids, hub scores, the work counter, and
+    // for the general search with a hub sample, every query's seed set
     const size_t qf = static_cast<size_t>(nq) * 64 * 4, qb = static_cast<size_t>(nq) * 64 * 2;
     const size_t hb = static_cast<size_t>(nm) * 4;
+    const size_t sb = one_launch ? 0 : static_cast<size_t>(nq) * m->n_hub_seeds * 4;
     void *scr = nullptr;
-    st = scratch_alloc(idx, qf + qb + 2 * hb + 256, s, &scr);
+    st = scratch_alloc(idx, qf + qb + 2 * hb + 256 + sb, s, &scr);
     if (st != ANN_OK) {
         cudaSetDevice(prev);
         return st;
@@ -1229,9 +1308,7 @@ ann_status ann_select_entries(ann_index *idx, const void *d_queries, int64_t nq,
     int32_t *hid = reinterpret_cast<int32_t *>(static_cast<uint8_t *>(scr) + qf + qb);
     float *hsc = reinterpret_cast<float *>(static_cast<uint8_t *>(scr) + qf + qb + hb);
     st = launch_tower(m, X, nq, qhat, qbf, nullptr, nullptr, nullptr, idx->d_status, s);
-    if (st == ANN_OK && L_hub <= kNavMaxPool && m->s <= 32 && nq <= INT32_MAX) {
-        // the hub-graph search in one launch (pools of up to 64 hubs; a
-        // 32-bit work counter)
+    if (st == ANN_OK && one_launch) {
         const int bm_words = (m->H + 127) / 128 * 4;
         const size_t per_warp = 256 + 4 * static_cast<size_t>(bm_words);
         const size_t smem = per_warp * kNavWarps;
@@ -1249,8 +1326,8 @@ ann_status ann_select_entries(ann_index *idx, const void *d_queries, int64_t nq,
                 e = cudaMemsetAsync(counter, 0, 4, s);
             if (e == cudaSuccess) {
                 kern<<<static_cast<unsigned>(blocks), 32 * kNavWarps, smem, s>>>(
-                    qhat, nq, m->Eb, m->H, m->hub_graph, m->s, m->hub_entry, L_hub, m_seeds, m->hub_nodes,
-                    idx->medoid, bm_words, counter, d_entry);
+                    qhat, nq, m->Eb, m->H, m->hub_graph, m->s, m->hub_seeds, std::max(m->n_hub_seeds, 1), L_hub,
+                    m_seeds, m->hub_nodes, idx->medoid, bm_words, counter, d_entry);
                 e = cudaGetLastError();
             }
         }
@@ -1265,11 +1342,21 @@ ann_status ann_select_entries(ann_index *idx, const void *d_queries, int64_t nq,
         Ls.qbytes = 64 * 4;
         Ls.nq = nq;
         Ls.entries = nullptr;
+        if (m->n_hub_seeds > 0) {
+            int32_t *seeds = reinterpret_cast<int32_t *>(static_cast<uint8_t *>(scr) + qf + qb + 2 * hb + 256);
+            const int64_t ns = nq * m->n_hub_seeds;
+            broadcast_hub_seeds<<<static_cast<unsigned>((ns + 255) / 256), 256, 0, s>>>(m->hub_seeds,
+                                                                                       m->n_hub_seeds, ns, seeds);
+            st = cuda_status(cudaGetLastError());
+            Ls.entries = seeds;
+            p.n_entries = m->n_hub_seeds;
+        }
         Ls.p = &p;
         Ls.ids = hid;
         Ls.dists = hsc;
         Ls.stats = nullptr;
-        st = launch_search(m->hub_index, Ls, s);
+        if (st == ANN_OK)
+            st = launch_search(m->hub_index, Ls, s);
         if (st == ANN_OK) {
             map_hub_seeds<<<static_cast<unsigned>((nm + 255) / 256), 256, 0, s>>>(hid, nq, m_seeds, m->hub_nodes,
                                                                                  idx->medoid, d_entry);

@@ -26,6 +26,11 @@ struct ann_entry_model {
     int32_t *hub_nodes = nullptr;            // [H] node ids
     int32_t *hub_graph = nullptr;            // [H][s]
     int32_t hub_entry = 0;
+    // the hubs the hub-graph search starts from (Algorithm 1's initial node
+    // set), device [ANN_MAX_SEEDS]: the caller's sample (n_hub_seeds > 0) or,
+    // with n_hub_seeds = 0, hub_entry alone in slot 0
+    int32_t *hub_seeds = nullptr;
+    int n_hub_seeds = 0;
     ann_index *hub_index = nullptr;          // BF16 / IP index over Eb and hub_graph
 };
 

@@ -223,6 +223,12 @@ def sample_rows(n, m, seed):
     return np.sort(_rng(seed).choice(n, size=m, replace=False)).astype(np.int64)
 
 
+def hub_sample(n_hubs, m, seed=SEED_BASE + 102):
+    """m distinct hub indices out of n_hubs, in draw order: the random node
+    sample that starts the hub-graph search (Algorithm 1's initial set)."""
+    return _rng(seed).permutation(n_hubs)[:min(m, n_hubs)].astype(np.int32)
+
+
 def train_batches(n_train, batch, epochs, seed):
     """Per-epoch random permutations of the training queries."""
     rng = _rng(seed)

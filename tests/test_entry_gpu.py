@@ -173,6 +173,51 @@ def test_nav_search_matches_oracle(setup, L_hub):
     assert S[r, oi[:, 0]].mean() - S[r, chosen].mean() <= 1e-4
 
 
+@pytest.mark.parametrize("L_hub,n_start", [(8, 32), (24, 8), (32, 32), (40, 17), (64, 32), (100, 20)])
+def test_nav_from_hub_sample_matches_oracle(setup, L_hub, n_start):
+    # Algorithm 1 started from a sample of the hubs (its initial node set,
+    # with one hub repeated: it counts once), in the one-launch kernel (pools
+    # up to 64, samples larger or smaller than the pool) and in the general
+    # search on the hub index (pool 100), against the oracle's search of the
+    # hub graph from the same seed set
+    start = synth.hub_sample(300, n_start, seed=40 + L_hub)
+    start[-1] = start[0]
+    before, _ = _select(setup, ann.ENTRY_LEARNED_NAV, L_hub=L_hub)
+    ann.ann_set_hub_seeds(setup["h"], start)
+    try:
+        ent, _ = _select(setup, ann.ENTRY_LEARNED_NAV, L_hub=L_hub)
+    finally:
+        ann.ann_set_hub_seeds(setup["h"], None)
+    Eb = _eb(setup["W"][4]).astype(np.float32)
+    ref_q = _oracle_qhat(setup["q"], setup["W"])
+    seeds = np.broadcast_to(start, (len(ref_q), n_start))
+    oi, _, _, _ = oracle.search(Eb, setup["adj"], ref_q, seeds, L_hub, 1, metric=oracle.IP)
+    hub_of = {int(n): i for i, n in enumerate(setup["hub_nodes"])}
+    chosen = np.array([hub_of[int(e)] for e in ent])
+    assert (chosen == oi[:, 0]).mean() >= 0.99
+    S = ref_q @ Eb.astype(np.float64).T
+    r = np.arange(len(S))
+    assert S[r, oi[:, 0]].mean() - S[r, chosen].mean() <= 1e-4
+    # without the sample the walk starts from the entry hub again, as before
+    after, _ = _select(setup, ann.ENTRY_LEARNED_NAV, L_hub=L_hub)
+    assert (after == before).all()
+
+
+def test_hub_sample_errors(setup):
+    h = setup["h"]
+    for bad in ([0, 300], [-1], list(range(33))):
+        with pytest.raises(ann.AnnError) as ei:
+            ann.ann_set_hub_seeds(h, bad)
+        assert ei.value.status == ann.ERR_INVALID_ARG
+    h2 = ann.ann_index_create(setup["base"], setup["graph"], setup["medoid"], ann.F32, ann.L2)
+    try:
+        with pytest.raises(ann.AnnError) as ei:
+            ann.ann_set_hub_seeds(h2, [0, 1])
+        assert ei.value.status == ann.ERR_UNSUPPORTED
+    finally:
+        ann.ann_free_index(h2)
+
+
 def test_nav_with_two_thousand_hubs_matches_oracle(setup):
     # a hub set seven times larger (a wider visited bitmap per warp), two
     # pool sizes, against the oracle's walk
