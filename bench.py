@@ -6,8 +6,9 @@ Default workload (`--workload shift`): the shifted-query 1M x 128 fp32 config.
 Setup (untimed, all on the GPU through libann): the synthetic workload, the
 proximity graph (exact 64-NN + RNG pruning, R = 32), exact ground truth, 1,024
 k-means hubs, label-mode search costs for 100,000 training queries, the label
-rule (t_pos = 3, t_neg = 15) and the contrastive training of the two-tower
-entry model (Adam, batch 8,192).
+rule (t_pos = 3, t_neg = 15), the contrastive training of the two-tower
+entry model (Adam, batch 8,192) and its hub graph (undirected: each hub's 8
+most cosine-similar hubs and the hubs that list it, at most 16; --hub-graph).
 
 One step = one batch of the evaluation queries through the public path:
 ann_select_entry (query tower, then the hub-graph search or the exhaustive
@@ -172,12 +173,16 @@ def parse():
     ap.add_argument("--lr", type=float, default=5e-5)
     ap.add_argument("--tau", type=float, default=0.07)
     ap.add_argument("--cand", type=int, default=64, help="hubs searched per training query")
-    ap.add_argument("--l-hub", type=int, default=32)
+    ap.add_argument("--l-hub", type=int, default=32, help="pool size of the hub-graph search")
     ap.add_argument("--hub-seeds", type=int, default=0,
                     help="hubs in the sample the hub-graph search starts from (0: the entry hub alone)")
+    ap.add_argument("--hub-graph", default="8:16",
+                    help="s:max_degree of the hub graph: each hub's s most similar hubs, directed "
+                         "(max_degree 0) or undirected with at most max_degree neighbours")
     ap.add_argument("--nav-sweep", default="",
-                    help="comma list of L_hub:sample pairs: the hub-graph mode measured at each (its L*, "
-                         "evaluations, QPS with the exhaustive mode's tuned sizes, entry selection time)")
+                    help="comma list of L_hub:sample[:s:max_degree] items: the hub-graph mode measured at "
+                         "each (its L*, evaluations, QPS with the exhaustive mode's tuned sizes, entry "
+                         "selection time)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--capture", action="store_true",
                     help="run the first measured mode's search in a fixed sequence for a profiler capture "
@@ -874,6 +879,12 @@ def measure_mode(run, torch, ann, W, args, targets):
                 entries=None if run.mode == "medoid" else run.entry.cpu().numpy())
 
 
+def set_hub_graph(W, ann, spec):
+    """Rebuild the hub graph from an "s:max_degree" string."""
+    s_nn, _, md = spec.partition(":")
+    ann.ann_build_hub_graph(W["h"], int(s_nn), int(md or 0))
+
+
 def set_hub_sample(W, ann, synth, n):
     """The hub-graph search starts from n hubs drawn at random (0: the entry hub)."""
     ann.ann_set_hub_seeds(W["h"], synth.hub_sample(W["H"], n) if n > 0 else None)
@@ -898,10 +909,16 @@ def nav_sweep(W, torch, ann, synth, args, dev, targets, ref):
     sizes (speed-only knobs, picked at a nearby L)."""
     out = []
     l_hub0 = args.l_hub
+    graph = args.hub_graph
     for item in args.nav_sweep.split(","):
-        lh, _, ns = item.partition(":")
-        args.l_hub = int(lh)
-        set_hub_sample(W, ann, synth, int(ns or 0))
+        parts = item.split(":")
+        lh, ns = int(parts[0]), int(parts[1]) if len(parts) > 1 else 0
+        g = ":".join(parts[2:4]) if len(parts) > 2 else args.hub_graph
+        if g != graph:
+            set_hub_graph(W, ann, g)
+            graph = g
+        args.l_hub = lh
+        set_hub_sample(W, ann, synth, ns)
         run = Runner(W, torch, ann, args, "learned")
         Lstar, _, per = sweep(run, torch, ann, W, targets)
         if ref["run"].tuned.get(ref["L"]) is not None:
@@ -915,11 +932,13 @@ def nav_sweep(W, torch, ann, synth, args, dev, targets, ref):
         st = run.stats.cpu().numpy().astype(np.int64)
         tm, _, _ = timed(run, torch, ann, argparse.Namespace(warmup=3, steps=100), Lstar, 1, dev,
                          lanes=args.lanes)
-        out.append(dict(l_hub=args.l_hub, sample=int(ns or 0), L=Lstar,
+        out.append(dict(l_hub=args.l_hub, sample=ns, hub_graph=graph, L=Lstar,
                         recall=recall(run.ids.cpu().numpy(), W["gt"], run.k),
                         evals=float(st[:, 0].mean()), qps=run.nq * 100 / (tm / 1e3),
                         entry_ms=entry_ms(run, torch)))
     args.l_hub = l_hub0
+    if graph != args.hub_graph:
+        set_hub_graph(W, ann, args.hub_graph)
     set_hub_sample(W, ann, synth, args.hub_seeds)
     return out
 
@@ -1099,6 +1118,8 @@ def run_gpu(args):
     learned = build_learned(W, args, torch, ann, synth, dev) if spec["learned"] else None
     if learned:
         W["H"] = learned["H"]
+        if args.hub_graph != "16:0":  # the graph the trainer attaches
+            set_hub_graph(W, ann, args.hub_graph)
         set_hub_sample(W, ann, synth, args.hub_seeds)
     targets = spec["targets"]
 
@@ -1181,7 +1202,8 @@ def run_gpu(args):
                "evals_per_query": R["evals"], "hops_per_query": R["hops"],
                "per_target": {str(t): v for t, v in R["per_target"].items()},
                "tuned": R["tune"], "sweep": R["sweep"], "other_entry_modes": others,
-               "l_hub": args.l_hub, "hub_sample": args.hub_seeds, "lanes": n_lanes,
+               "l_hub": args.l_hub, "hub_sample": args.hub_seeds, "hub_graph": args.hub_graph,
+               "lanes": n_lanes,
                "l2": "inputs larger than L2 (129 MB), no flush" if big
                else "base smaller than L2: an L2-resident parity config",
                "graph_build_s": W["t_build"], "repairs": W["repairs"], "learned": learned,

@@ -419,6 +419,26 @@ ann_status ann_get_entry_model(const ann_index *idx, float *W1, float *b1, float
                                int32_t *hub_entry);
 
 /*
+ * Rebuild the attached model's hub graph (Sec. 4.3: every hub linked to its
+ * s most cosine-similar hubs).  Two readings of "connect edges":
+ *   max_degree = 0   directed: row i lists hub i's s_nn most similar other
+ *                    hubs (what ann_set_entry_model builds); row width s_nn
+ *   max_degree >= s  undirected: hubs u and v are linked when either lists
+ *                    the other; row i lists its neighbours in decreasing
+ *                    cosine (smaller index on ties), at most max_degree of
+ *                    them, padded with -1; row width max_degree
+ *   s_nn 1..32 and < n_hubs; max_degree 0 or s_nn..32.
+ * The similarities are inner products of the normalised FP32 embeddings (the
+ * undirected ordering in double on the host).  The hub-graph index is
+ * rebuilt; the entry hub and the hub sample (ann_set_hub_seeds) are kept.
+ * ann_get_entry_model then returns rows of the new width.  Blocking: waits
+ * for the device first.  ANN_ERR_UNSUPPORTED without a model,
+ * ANN_ERR_INVALID_ARG for sizes out of range, ANN_ERR_OOM.  After a failure
+ * the hub-graph mode reports ANN_ERR_UNSUPPORTED until a rebuild succeeds.
+ */
+ann_status ann_build_hub_graph(ann_index *idx, int32_t s_nn, int32_t max_degree, void *stream);
+
+/*
  * The sample of hubs the hub-graph search (ANN_ENTRY_LEARNED_NAV) starts
  * from.  Algorithm 1 (Sec. 2.1) starts its pool from a random sample of the
  * graph's nodes; on the high-tier graph of Sec. 4.3 that sample is this list.

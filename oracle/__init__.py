@@ -264,6 +264,29 @@ def hub_graph(emb, s):
     return adj, int(ent[0])
 
 
+def hub_graph_undirected(emb, s, max_degree):
+    """Undirected reading of the high-tier hub graph (Sec. 4.3): hubs u and v
+    are linked when v is among u's s most cosine-similar hubs or u among v's
+    (the directed lists of ``hub_graph``).  Row i holds i's neighbours in
+    decreasing cosine (float64, ties to the smaller index), at most
+    max_degree of them, padded with -1.  Returns (adjacency [H, max_degree],
+    entry hub)."""
+    adj, ent = hub_graph(emb, s)
+    e = np.asarray(emb, np.float64)
+    en = e / np.linalg.norm(e, axis=1, keepdims=True)
+    H = len(e)
+    nbrs = [set() for _ in range(H)]
+    for i in range(H):
+        for j in adj[i]:
+            nbrs[i].add(int(j))
+            nbrs[int(j)].add(i)
+    out = np.full((H, max_degree), -1, np.int32)
+    for i in range(H):
+        lst = sorted(nbrs[i], key=lambda j: (-float(en[i] @ en[j]), j))[:max_degree]
+        out[i, :len(lst)] = lst
+    return out, ent
+
+
 def recall_at_k(found_ids, truth_ids, k):
     """recall@k = |R ∩ R'| / k averaged over queries (Sec. 2.1, Eq. recall)."""
     f = np.asarray(found_ids)[:, :k]

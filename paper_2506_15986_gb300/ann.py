@@ -91,6 +91,7 @@ def load_library(path: str | None = None):
         "ann_get_entry_model": ([_p] + [_p] * 7 + [_c.POINTER(i32)], i32),
         "ann_select_entry": ([_p, _p, i64, i32, i32, _p, _p, _p], i32),
         "ann_set_hub_seeds": ([_p, _p, i32], i32),
+        "ann_build_hub_graph": ([_p, i32, i32, _p], i32),
         "ann_select_entries": ([_p, _p, i64, i32, i32, i32, _p, _p, _p], i32),
         "ann_trainer_create": ([i32, i32, i32, _p, _p, _p, _p, _p, i64, _c.c_float, _c.c_float,
                                 _c.c_float, _c.c_float, _c.c_float, pp], i32),
@@ -284,6 +285,13 @@ def ann_get_entry_model(h, W1=None, b1=None, W2=None, b2=None, hub_emb=None, hub
                                               _ptr(hub_emb), _ptr(hub_nodes), _ptr(hub_graph),
                                               ctypes.byref(e)), "ann_get_entry_model")
     return e.value
+
+
+def ann_build_hub_graph(h, s_nn, max_degree=0, stream=None):
+    """Rebuild the model's hub graph: directed s_nn nearest (max_degree 0) or
+    undirected, at most max_degree neighbours per hub."""
+    _check(load_library().ann_build_hub_graph(h, int(s_nn), int(max_degree), _stream(stream)),
+           "ann_build_hub_graph")
 
 
 def ann_set_hub_seeds(h, seeds):

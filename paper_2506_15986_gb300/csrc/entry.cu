@@ -20,6 +20,7 @@
 
 #include <algorithm>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "entry.h"
@@ -1082,12 +1083,14 @@ ann_status build_hub_index(ann_index *idx, ann_entry_model *m, const int32_t *hu
         if (e != cudaSuccess)
             return cuda_status(e);
     }
-    // the start list of the hub-graph search: the entry hub until a sample is set
-    if (!m->hub_seeds)
+    // the start list of the hub-graph search: the entry hub until a sample is
+    // set (a rebuilt graph keeps the model's list)
+    if (!m->hub_seeds) {
         m->hub_seeds = dev_alloc<int32_t>(ANN_MAX_SEEDS, e);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(m->hub_seeds, &m->hub_entry, 4, cudaMemcpyHostToDevice, s);
-    m->n_hub_seeds = 0;
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(m->hub_seeds, &m->hub_entry, 4, cudaMemcpyHostToDevice, s);
+        m->n_hub_seeds = 0;
+    }
     if (e == cudaSuccess)
         e = cudaStreamSynchronize(s);
     if (e != cudaSuccess)
@@ -1213,6 +1216,88 @@ ann_status ann_get_entry_model(const ann_index *idx, float *W1, float *b1, float
     return cuda_status(e);
 }
 
+ann_status ann_build_hub_graph(ann_index *idx, int32_t s_nn, int32_t max_degree, void *stream)
+{
+    if (!idx)
+        return ANN_ERR_INVALID_ARG;
+    ann_entry_model *m = idx->model;
+    if (!m)
+        return ANN_ERR_UNSUPPORTED;
+    const int H = m->H;
+    if (s_nn < 1 || s_nn > 32 || s_nn >= H || (max_degree != 0 && (max_degree < s_nn || max_degree > 32)))
+        return ANN_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(idx->device);
+    const int width = max_degree ? max_degree : s_nn;
+    // each hub's s most cosine-similar other hubs (inner products of the
+    // normalised embeddings, smaller index on ties)
+    cudaError_t e = cudaSuccess;
+    int32_t *d_ids = dev_alloc<int32_t>(static_cast<size_t>(H) * s_nn, e);
+    float *d_sc = dev_alloc<float>(static_cast<size_t>(H) * s_nn, e);
+    ann_status st = cuda_status(e);
+    if (st == ANN_OK)
+        st = knn_exact(m->En, H, 64, ANN_F32, ANN_IP, m->En, H, s_nn, true, d_ids, d_sc, s);
+    std::vector<int32_t> nn(static_cast<size_t>(H) * s_nn);
+    std::vector<float> En;
+    if (st == ANN_OK)
+        st = cuda_status(cudaMemcpyAsync(nn.data(), d_ids, nn.size() * 4, cudaMemcpyDeviceToHost, s));
+    if (st == ANN_OK && max_degree) {
+        En.resize(static_cast<size_t>(H) * 64);
+        st = cuda_status(cudaMemcpyAsync(En.data(), m->En, En.size() * 4, cudaMemcpyDeviceToHost, s));
+    }
+    if (st == ANN_OK)
+        st = cuda_status(cudaStreamSynchronize(s));
+    cudaFree(d_ids);
+    cudaFree(d_sc);
+    std::vector<int32_t> rows(static_cast<size_t>(H) * width, -1);
+    if (st == ANN_OK && !max_degree) {
+        rows = nn;
+    } else if (st == ANN_OK) {
+        // undirected edges: u and v are linked when either lists the other;
+        // a hub's neighbours in decreasing cosine (smaller index on ties), at
+        // most max_degree of them (rows padded with -1)
+        std::vector<std::vector<int32_t>> adj(H);
+        for (int i = 0; i < H; ++i)
+            for (int r = 0; r < s_nn; ++r) {
+                const int32_t j = nn[static_cast<size_t>(i) * s_nn + r];
+                if (j < 0 || j >= H || j == i)
+                    continue;
+                adj[i].push_back(j);
+                adj[j].push_back(i);
+            }
+        for (int i = 0; i < H; ++i) {
+            std::vector<int32_t> &a = adj[i];
+            std::sort(a.begin(), a.end());
+            a.erase(std::unique(a.begin(), a.end()), a.end());
+            std::vector<std::pair<double, int32_t>> by(a.size());
+            for (size_t t = 0; t < a.size(); ++t) {
+                double c = 0.0;
+                for (int k = 0; k < 64; ++k)
+                    c += static_cast<double>(En[static_cast<size_t>(i) * 64 + k]) *
+                         static_cast<double>(En[static_cast<size_t>(a[t]) * 64 + k]);
+                by[t] = {-c, a[t]};
+            }
+            std::sort(by.begin(), by.end());
+            for (size_t t = 0; t < by.size() && t < static_cast<size_t>(width); ++t)
+                rows[static_cast<size_t>(i) * width + t] = by[t].second;
+        }
+    }
+    if (st == ANN_OK) {
+        // entry selections still in flight (on any stream) read the old graph
+        st = cuda_status(cudaDeviceSynchronize());
+    }
+    if (st == ANN_OK) {
+        cudaFree(m->hub_graph);
+        m->hub_graph = nullptr;
+        m->s = width;
+        st = build_hub_index(idx, m, rows.data(), m->hub_entry, s);
+    }
+    cudaSetDevice(prev);
+    return st;
+}
+
 ann_status ann_set_hub_seeds(ann_index *idx, const int32_t *seeds, int32_t n)
 {
     if (!idx || n < 0 || n > ANN_MAX_SEEDS || (n > 0 && !seeds))
@@ -1280,6 +1365,10 @@ ann_status ann_select_entries(ann_index *idx, const void *d_queries, int64_t nq,
     if (!m || (mode == ANN_ENTRY_LEARNED_NAV && (L_hub < m_seeds || L_hub > ANN_MAX_L))) {
         cudaSetDevice(prev);
         return m ? ANN_ERR_INVALID_ARG : ANN_ERR_UNSUPPORTED;
+    }
+    if (mode == ANN_ENTRY_LEARNED_NAV && (!m->hub_graph || !m->hub_index)) {
+        cudaSetDevice(prev);
+        return ANN_ERR_UNSUPPORTED;  // a failed hub-graph rebuild left no graph
     }
     const Operand X{d_queries, idx->dtype == ANN_U8 ? OP_U8 : OP_F32, idx->dim, 1, nq, idx->dim, nullptr};
     if (mode == ANN_ENTRY_LEARNED_EXHAUSTIVE) {

@@ -203,6 +203,54 @@ def test_nav_from_hub_sample_matches_oracle(setup, L_hub, n_start):
     assert (after == before).all()
 
 
+@pytest.mark.parametrize("s_nn,max_degree", [(8, 0), (6, 12), (8, 32)])
+def test_undirected_hub_graph_and_walk_match_oracle(setup, s_nn, max_degree):
+    # the hub graph rebuilt on the GPU (directed, or undirected with a degree
+    # cap: rows of -1-padded neighbours) against the oracle's rule, and the
+    # hub-graph search over it against the oracle's walk over the oracle's
+    # graph, in the one-launch kernel (two pool sizes) and the general search
+    W1, b1, W2, b2, E = setup["W"]
+    h = ann.ann_index_create(setup["base"], setup["graph"], setup["medoid"], ann.F32, ann.L2)
+    try:
+        ann.ann_set_entry_model(h, 128, W1, b1, W2, b2, setup["hub_nodes"], E, 8, hub_graph=setup["adj"],
+                                hub_entry=setup["ent"])
+        ann.ann_build_hub_graph(h, s_nn, max_degree)
+        width = max_degree or s_nn
+        got = np.empty((300, width), np.int32)
+        ent = ann.ann_get_entry_model(h, hub_graph=got)
+        assert ent == setup["ent"]
+        if max_degree:
+            ref, _ = oracle.hub_graph_undirected(E.astype(np.float64), s_nn, max_degree)
+        else:
+            ref, _ = oracle.hub_graph(E.astype(np.float64), s_nn)
+        assert (got == ref).all(1).mean() >= 0.99
+        Eb = _eb(E).astype(np.float32)
+        ref_q = _oracle_qhat(setup["q"], setup["W"])
+        hub_of = {int(n): i for i, n in enumerate(setup["hub_nodes"])}
+        for L_hub in (16, 40, 80):
+            e, _ = _select(dict(setup, h=h), ann.ENTRY_LEARNED_NAV, L_hub=L_hub)
+            oi, _, _, _ = oracle.search(Eb, ref, ref_q, setup["ent"], L_hub, 1, metric=oracle.IP)
+            chosen = np.array([hub_of[int(x)] for x in e])
+            assert (chosen == oi[:, 0]).mean() >= 0.99
+    finally:
+        ann.ann_free_index(h)
+
+
+def test_hub_graph_rebuild_errors(setup):
+    h = setup["h"]
+    for s_nn, md in ((0, 0), (33, 0), (300, 0), (8, 7), (8, 33)):
+        with pytest.raises(ann.AnnError) as ei:
+            ann.ann_build_hub_graph(h, s_nn, md)
+        assert ei.value.status == ann.ERR_INVALID_ARG
+    h2 = ann.ann_index_create(setup["base"], setup["graph"], setup["medoid"], ann.F32, ann.L2)
+    try:
+        with pytest.raises(ann.AnnError) as ei:
+            ann.ann_build_hub_graph(h2, 8, 0)
+        assert ei.value.status == ann.ERR_UNSUPPORTED
+    finally:
+        ann.ann_free_index(h2)
+
+
 def test_hub_sample_errors(setup):
     h = setup["h"]
     for bad in ([0, 300], [-1], list(range(33))):

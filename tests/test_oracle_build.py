@@ -165,6 +165,44 @@ def test_hub_graph_hand_case():
     assert adj.ravel().tolist() == [1, 0, 1, 2]
 
 
+def test_undirected_hub_graph_hand_case():
+    # the four vectors above (s = 1): directed 0->1, 1->0, 2->1, 3->2, so the
+    # undirected edges are {0,1}, {1,2}, {2,3}.  Rows by decreasing cosine:
+    # 0: [1]; 1: [0 (cos 10deg), 2 (cos 80deg)]; 2: [1 (cos 80deg), 3 (cos 90deg)];
+    # 3: [2]; width 3, padded with -1
+    a = np.deg2rad([0, 10, 90, 180])
+    E = np.stack([np.cos(a), np.sin(a)], 1)
+    adj, ent = oracle.hub_graph_undirected(E, 1, 3)
+    assert adj.tolist() == [[1, -1, -1], [0, 2, -1], [1, 3, -1], [2, -1, -1]]
+    # a cap of one keeps the most similar neighbour only
+    adj1, _ = oracle.hub_graph_undirected(E, 1, 1)
+    assert adj1.ravel().tolist() == [1, 0, 1, 2]
+    assert ent == oracle.hub_graph(E, 1)[1]
+
+
+def test_undirected_hub_graph_matches_bruteforce():
+    # against the definition from a brute-force cosine ranking: v in N(u) iff
+    # v is among u's s nearest or u among v's; symmetric without a cap; each
+    # capped row is the prefix of the uncapped one
+    rng = np.random.default_rng(3)
+    E = rng.standard_normal((80, 6))
+    s = 4
+    En = E / np.linalg.norm(E, axis=1, keepdims=True)
+    C = En @ En.T
+    top = [sorted([j for j in range(80) if j != i], key=lambda j: (-C[i, j], j))[:s] for i in range(80)]
+    full, _ = oracle.hub_graph_undirected(E, s, 80)
+    for i in range(80):
+        want = {j for j in top[i]} | {j for j in range(80) if i in top[j]}
+        row = [j for j in full[i] if j >= 0]
+        assert row == sorted(want, key=lambda j: (-C[i, j], j))
+        assert all(i in full[j] for j in row)
+    capped, _ = oracle.hub_graph_undirected(E, s, 6)
+    for i in range(80):
+        row = [j for j in full[i] if j >= 0][:6]
+        assert [j for j in capped[i] if j >= 0] == row
+        assert (capped[i, len(row):] == -1).all()
+
+
 def test_labels_rule_hand_case():
     I = oracle.INT32_MAX
     # one query, 5 searched hubs (indices 4,0,1,2,3 in the candidate list)
