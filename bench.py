@@ -947,7 +947,8 @@ def precision_report(W, torch, ann, args, dev):
     """fp16 storage and int8 storage with a per-row scale, each with and
     without the exact fp32 rerank, against fp32 storage (k = 10 and 100), with
     the distance error of each against float64 recomputation from the fp32
-    rows."""
+    rows (relative to the distance under L2, to |x| |q| under the inner
+    product)."""
     base = W["w"]["base"]
     n, dim = base.shape
     h16 = ann.ann_index_create(base.astype(np.float16), W["graph"], W["medoid"], ann.F16, W["metric"],
@@ -975,9 +976,16 @@ def precision_report(W, torch, ann, args, dev):
                 rel = []
                 for i in range(0, len(q), max(1, len(q) // 100)):
                     ok = ids[i] >= 0
-                    diff = base[ids[i][ok]].astype(np.float64) - q[i]
-                    d64 = (diff * diff).sum(1)
-                    rel.append(np.abs(d[i][ok] - d64) / np.maximum(d64, 1e-30))
+                    x = base[ids[i][ok]].astype(np.float64)
+                    if W["metric"] == ann.IP:
+                        # -<x, q>, its error relative to |x| |q| (inner products
+                        # near zero have no meaningful relative error)
+                        d64 = -(x @ q[i])
+                        scale = np.linalg.norm(x, axis=1) * np.linalg.norm(q[i])
+                    else:
+                        d64 = ((x - q[i]) ** 2).sum(1)
+                        scale = d64
+                    rel.append(np.abs(d[i][ok] - d64) / np.maximum(scale, 1e-30))
                 rel = np.concatenate(rel)
                 out[f"{name}_k{k}"] = dict(L=Lstar, recall=recall(ids, W["gt"], k),
                                            qps=run.nq * 20 / (tm / 1e3),
