@@ -71,3 +71,16 @@ def test_capture_and_knob_options(monkeypatch):
         for key in ("digest", "entry", "L", "nq", "hash_bits", "stage_rows", "team", "spill_bits", "gather",
                     "visited_l2", "group_entries", "bytes"):
             assert key in mt, key
+
+
+def test_hub_graph_options(monkeypatch):
+    # the hub-graph mode's defaults: the undirected s = 8 graph capped at 16
+    # neighbours, a pool of 32, no start sample
+    monkeypatch.setattr("sys.argv", ["bench.py"])
+    args = bench.parse()
+    assert args.hub_graph == "8:16" and args.l_hub == 32 and args.hub_seeds == 0 and args.nav_sweep == ""
+    monkeypatch.setattr("sys.argv", ["bench.py", "--hub-graph", "16:0", "--l-hub", "16", "--hub-seeds", "32",
+                                     "--nav-sweep", "16:0:16:32,32:32"])
+    args = bench.parse()
+    assert args.hub_graph == "16:0" and args.l_hub == 16 and args.hub_seeds == 32
+    assert [item.split(":") for item in args.nav_sweep.split(",")] == [["16", "0", "16", "32"], ["32", "32"]]
