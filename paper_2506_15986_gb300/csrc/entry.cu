@@ -771,22 +771,50 @@ __device__ __forceinline__ void nav_insert(uint64_t (&pool)[NP], uint64_t cand, 
     }
 }
 
+// <q, e> over the 8 coordinates 8 sub .. 8 sub + 7 of a BF16 hub row, q in
+// registers (qr), one FP32 accumulator in coordinate order
+__device__ __forceinline__ float hub_dot8(const float (&qr)[8], const __nv_bfloat16 *row, int sub)
+{
+    const uint4 x = __ldg(reinterpret_cast<const uint4 *>(row) + sub);
+    const float2 f0 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&x.x));
+    const float2 f1 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&x.y));
+    const float2 f2 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&x.z));
+    const float2 f3 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&x.w));
+    float a = f0.x * qr[0];
+    a = fmaf(f0.y, qr[1], a);
+    a = fmaf(f1.x, qr[2], a);
+    a = fmaf(f1.y, qr[3], a);
+    a = fmaf(f2.x, qr[4], a);
+    a = fmaf(f2.y, qr[5], a);
+    a = fmaf(f3.x, qr[6], a);
+    return fmaf(f3.y, qr[7], a);
+}
+
 // NP keys per lane: pools of up to 32 * NP hubs (element r * 32 + lane in
 // pool[r]).
-// Registers are capped for eight 8-warp CTAs per SM with one key per lane
-// (six with two): the walk is latency-bound, so resident warps count more
-// than registers (no spills at 32 and 40 registers).
+// A step scores its fresh neighbours four at a time, eight lanes per
+// neighbour: lane 8g + sub keeps coordinates 8 sub .. 8 sub + 7 of q_hat in
+// registers, reads the matching 16 bytes of the hub row and the group adds
+// its eight partial products by three xor-shuffles.  So q_hat is read from
+// shared memory once per query instead of once per scored neighbour, and
+// only fresh neighbours are scored (their ids are compacted through shared
+// memory first).
+// Registers are capped at 40 (six 8-warp CTAs per SM; no spills with one or
+// two keys per lane): the eight q_hat coordinates per lane do not fit the 32
+// that eight CTAs would leave.
 template <int NP>
-__global__ void __launch_bounds__(32 * kNavWarps, NP == 1 ? 8 : 6)
+__global__ void __launch_bounds__(32 * kNavWarps, 6)
     hub_nav_kernel(const float *qhat, int64_t nq, const __nv_bfloat16 *Eb, int H, const int32_t *hgraph, int s,
                    const int32_t *start, int n_start, int L, int m_seeds, const int32_t *hub_nodes, int32_t medoid,
                    int bm_words, unsigned *counter, int32_t *out)
 {
     extern __shared__ __align__(16) uint8_t nav_smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int per_warp = 256 + 4 * bm_words;
+    const int sub = lane & 7, grp = lane >> 3;
+    const int per_warp = 256 + 128 + 4 * bm_words;
     float *q = reinterpret_cast<float *>(nav_smem + wid * per_warp);
-    uint32_t *vis = reinterpret_cast<uint32_t *>(nav_smem + wid * per_warp + 256);
+    int32_t *fresh_ids = reinterpret_cast<int32_t *>(nav_smem + wid * per_warp + 256);
+    uint32_t *vis = reinterpret_cast<uint32_t *>(nav_smem + wid * per_warp + 384);
     for (;;) {
         // the next query from the launch's work queue (the grid holds only
         // resident warps, so the batch's last queries go to whichever warps
@@ -802,6 +830,13 @@ __global__ void __launch_bounds__(32 * kNavWarps, NP == 1 ? 8 : 6)
         for (int w = lane; w < bm_words; w += 32)
             vis[w] = 0u;
         __syncwarp();
+        float qr[8];
+        {
+            const float4 lo = reinterpret_cast<const float4 *>(q)[2 * sub];
+            const float4 hi = reinterpret_cast<const float4 *>(q)[2 * sub + 1];
+            qr[0] = lo.x, qr[1] = lo.y, qr[2] = lo.z, qr[3] = lo.w;
+            qr[4] = hi.x, qr[5] = hi.y, qr[6] = hi.z, qr[7] = hi.w;
+        }
         uint64_t pool[NP];
 #pragma unroll
         for (int r = 0; r < NP; ++r)
@@ -842,32 +877,30 @@ __global__ void __launch_bounds__(32 * kNavWarps, NP == 1 ? 8 : 6)
                 if (r == fr)
                     node = v;
             }
-            __syncwarp();
-            uint64_t cand = kKeyMax;
-            if (s <= 16) {
-                // two lanes per neighbour (j and j + 16), 32 coordinates each:
-                // the whole warp scores instead of s lanes
-                const int j = lane & 15, half = lane >> 4;
-                const int32_t nb = j < s ? __ldg(hgraph + static_cast<int64_t>(node) * s + j) : -1;
-                bool fresh = false;
-                if (half == 0 && nb >= 0 && nb < H) {
-                    const uint32_t bit = 1u << (nb & 31);
-                    fresh = !(atomicOr(&vis[nb >> 5], bit) & bit);
-                }
-                fresh = __shfl_sync(kFull, fresh, j);
-                float part = fresh ? hub_dot<4>(q + 32 * half, Eb + static_cast<int64_t>(nb) * 64 + 32 * half) : 0.f;
-                part += __shfl_xor_sync(kFull, part, 16);
-                if (half == 0 && fresh)
-                    cand = make_key(f32_to_ord(-part), nb);
-            } else {
-                const int32_t nb = lane < s ? __ldg(hgraph + static_cast<int64_t>(node) * s + lane) : -1;
-                if (nb >= 0 && nb < H) {
-                    const uint32_t bit = 1u << (nb & 31);
-                    if (!(atomicOr(&vis[nb >> 5], bit) & bit))
-                        cand = make_key(f32_to_ord(hub_score(q, Eb + static_cast<int64_t>(nb) * 64)), nb);
-                }
+            // the adjacency row (lane j holds neighbour j; -1 pads a short
+            // row), the visited test-and-set, the fresh ids compacted
+            const int32_t nb = lane < s ? __ldg(hgraph + static_cast<int64_t>(node) * s + lane) : -1;
+            bool fresh = false;
+            if (nb >= 0 && nb < H) {
+                const uint32_t bit = 1u << (nb & 31);
+                fresh = !(atomicOr(&vis[nb >> 5], bit) & bit);
             }
-            nav_insert<NP>(pool, cand, L, lane);
+            const unsigned fm = __ballot_sync(kFull, fresh);
+            if (fresh)
+                fresh_ids[__popc(fm & lanemask_lt())] = nb;
+            __syncwarp();
+            const int nf = __popc(fm);
+            for (int p = 0; p < nf; p += 4) {
+                const int i = p + grp;
+                const int32_t hb = i < nf ? fresh_ids[i] : -1;
+                float part = hb >= 0 ? hub_dot8(qr, Eb + static_cast<int64_t>(hb) * 64, sub) : 0.f;
+                part += __shfl_xor_sync(kFull, part, 1);
+                part += __shfl_xor_sync(kFull, part, 2);
+                part += __shfl_xor_sync(kFull, part, 4);
+                const uint64_t cand = hb >= 0 && sub == 0 ? make_key(f32_to_ord(-part), hb) : kKeyMax;
+                nav_insert<NP>(pool, cand, L, lane);
+            }
+            __syncwarp();
         }
         if (lane < m_seeds) {
             const int32_t hub = pool[0] != kKeyMax ? key_id(pool[0]) : -1;
@@ -1399,7 +1432,7 @@ ann_status ann_select_entries(ann_index *idx, const void *d_queries, int64_t nq,
     st = launch_tower(m, X, nq, qhat, qbf, nullptr, nullptr, nullptr, idx->d_status, s);
     if (st == ANN_OK && one_launch) {
         const int bm_words = (m->H + 127) / 128 * 4;
-        const size_t per_warp = 256 + 4 * static_cast<size_t>(bm_words);
+        const size_t per_warp = 256 + 128 + 4 * static_cast<size_t>(bm_words);
         const size_t smem = per_warp * kNavWarps;
         auto kern = L_hub <= 32 ? hub_nav_kernel<1> : hub_nav_kernel<2>;
         cudaError_t e =
