@@ -8,11 +8,15 @@
 // BF16) -> shared memory -> GEMM 2 without leaving the SM.
 // Hub side: each hub v has an embedding e_v; e_hat_v = e_v / |e_v| is kept as
 // BF16.  The entry of a query is the hub node of argmax_v q_hat . e_hat_v,
-// found either exhaustively (hub_argmax_kernel, a tcgen05 GEMM with a fused
-// per-row argmax epilogue) or by the greedy search of Algorithm 1 with the
-// inner-product metric over the high-tier hub graph (Sec. 4.3: every hub
-// linked to its s most cosine-similar hubs), which reuses the beam-search
-// kernel on a BF16 index of the hub embeddings.
+// found either exhaustively (entry_exhaustive_kernel: the tower and every
+// hub's score in one launch; hub_argmax_kernel: the scores alone, a tcgen05
+// GEMM with a fused per-row argmax epilogue) or by the greedy search of
+// Algorithm 1 with the inner-product metric over the high-tier hub graph
+// (Sec. 4.3: every hub linked to its s most cosine-similar hubs, as directed
+// lists or, after ann_build_hub_graph, as undirected edges): hub_nav_kernel
+// for pools of up to 64 hubs, the beam-search kernel on a BF16 index of the
+// hub embeddings for larger ones.  The walk starts from the entry hub or from
+// a caller-drawn sample of hubs (ann_set_hub_seeds).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
