@@ -18,7 +18,11 @@ bench trains on 100,000; fewer here to keep the test short).
   fp32 bar: >= 99.9 % of (query, rank) ids, distances within 1e-5 relative,
   recall@10 within 0.001, evaluation and expansion counts equal for >= 99 %.
 * Gain: over an L sweep, the learned entry reaches recall@10 >= 0.95 with
-  fewer distance evaluations per query than the medoid entry does."""
+  fewer distance evaluations per query than the medoid entry does.
+* Hub-graph search (the paper's entry path) on the undirected hub graph the
+  bench uses: its choices against the oracle's walk over the oracle's graph on
+  200 sampled queries, and its entries' evaluation cost against the
+  exhaustive argmax's at the same pool size."""
 import numpy as np
 import pytest
 
@@ -165,3 +169,38 @@ def test_trained_entry_needs_fewer_evaluations_than_the_medoid(learned):
     # needs fewer distance evaluations and fewer expansions
     assert el < em and hl < hm
     assert el <= 0.8 * em  # a clear gain, not noise: the bench measures 0.48x
+
+
+def test_hub_graph_search_on_the_undirected_graph(learned):
+    # the paper's entry path with the trained model at full size: the hub
+    # graph rebuilt undirected (each hub's 8 most similar hubs and the hubs
+    # that list it, at most 16, as the bench uses it), the walk at L_hub = 32.
+    # On 200 sampled queries the oracle walks its own graph of the trained
+    # embeddings from its own q_hat; then the walk's entries cost the search
+    # about what the exhaustive argmax's do
+    h, m = learned["h"], learned["model"]
+    ann.ann_build_hub_graph(h, 8, 16)
+    ent = torch.empty(NQ, dtype=torch.int32, device=DEV)
+    ann.ann_select_entry(h, learned["q"], NQ, ann.ENTRY_LEARNED_NAV, 32, ent)
+    assert ann.ann_sync_status(h) == ann.OK
+    ent_np = ent.cpu().numpy()
+    rng = np.random.default_rng(23)
+    sample = np.sort(rng.choice(NQ, 200, replace=False))
+    bf = ot.bf16_round
+    qo, _ = ot.tower_forward(bf(learned["w"]["queries"][sample]), bf(m["W1"]), m["b1"].astype(np.float64),
+                             bf(m["W2"]), m["b2"].astype(np.float64), round_hidden=bf)
+    En = m["E"].astype(np.float64) / np.linalg.norm(m["E"].astype(np.float64), axis=1, keepdims=True)
+    Eb = bf(En)
+    adj, entry_hub = oracle.hub_graph_undirected(m["E"].astype(np.float64), 8, 16)
+    oi, _, _, _ = oracle.search(Eb.astype(np.float32), adj, qo, entry_hub, 32, 1, metric=oracle.IP)
+    hub_of = {int(v): i for i, v in enumerate(m["nodes"])}
+    chosen = np.array([hub_of[int(e)] for e in ent_np[sample]])
+    assert (chosen == oi[:, 0]).mean() >= 0.98
+    S = qo @ Eb.T
+    r = np.arange(len(S))
+    assert S[r, oi[:, 0]].mean() - S[r, chosen].mean() <= 1e-4
+    # the same pool size for both entries: the walk's entries need at most 5 %
+    # more evaluations than the exhaustive argmax's (the bench measures 1 %)
+    _, _, st_nav = _search(learned, ent, 96)
+    _, _, st_exh = _search(learned, learned["ent"], 96)
+    assert st_nav[:, 0].mean() <= 1.05 * st_exh[:, 0].mean(), (st_nav[:, 0].mean(), st_exh[:, 0].mean())
