@@ -806,7 +806,7 @@ def end_to_end(run, torch, L, steps, world=1, dev="cpu", lanes=1):
     release_l2(run)
     return {"value": job_qps(run.nq, steps, world, dt_ms), "unit": "queries/s",
             "h2d_bytes_per_step": int(qh.numel() * qh.element_size()),
-            "d2h_bytes_per_step": int(ih[0].numel() * 4 + dh[0].numel() * 4), "lanes": n}
+            "d2h_bytes_per_step": int(ih[0].numel() * 4 + dh[0].numel() * 4), "lanes": n, "steps": steps}
 
 
 def cpu_baseline(W, L, entries=None, target_s=10.0, width=1, k=K_NN, one_thread=True):
@@ -1178,7 +1178,9 @@ def run_gpu(args):
                                 hops_per_query=r["hops"],
                                 per_target={str(t): v for t, v in r["per_target"].items()},
                                 search_ms=sm, tuned=r["tune"], sweep=r["sweep"])
-    e2e = end_to_end(R["run"], torch, R["L"], max(10, args.steps // 4), world, dev, lanes=args.lanes)
+    # at least 50 steps, so that the first batch's start and the last one's
+    # tail weigh little against the steady state the other steps measure
+    e2e = end_to_end(R["run"], torch, R["L"], max(50, args.steps // 4), world, dev, lanes=args.lanes)
     prec = precision_report(W, torch, ann, args, dev) if spec.get("precision") else None
     batching = batch_report(W, torch, ann, args, dev, ["medoid"] + ([head] if head != "medoid" else [])) \
         if spec.get("batching") else None
