@@ -195,6 +195,14 @@ def test_seed_sets():
     assert ids[0].tolist() == [7, 6]
     assert np.allclose(d[0], [0.2 ** 2, 1.2 ** 2])
     assert (int(ev[0]), int(hp[0])) == (5, 3)
+    # more seeds than the pool holds: every seed is evaluated (and visited),
+    # the pool keeps the L best.  Seeds 0, 2, 4, 6 with L = 2 and the query at
+    # 7.2: evaluated 0, 2, 4, 6, pool [6, 4]; expand 6: evaluates 5 and 7,
+    # pool [7, 6]; expand 7: nothing new; 6 is done -> stop.  evals = 4 + 2,
+    # hops = 2; node 1 and 3 never enter
+    ids, d, ev, hp = oracle.search(pts, adj, np.array([[7.2, 0.0]]), np.array([[0, 2, 4, 6]], np.int32), 2, 2)
+    assert ids[0].tolist() == [7, 6]
+    assert (int(ev[0]), int(hp[0])) == (6, 2)
     # L >= N on a connected graph: exact k-NN from any seed set
     ids, d, _, _ = oracle.search(base, g, q, np.array([[med, 3, 77]] * 12, np.int32), 400, 5)
     tid, td = oracle.knn(base, q, 5)
